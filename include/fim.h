@@ -1,0 +1,136 @@
+/*
+ * fim.h - C ABI of libfim, an exact isotropic median / percentile filter for one GPU.
+ *
+ * The filter is the one of "Fast Isotropic Median Filtering" (arXiv 2505.22938):
+ * out(x, y) is the value of 0-based rank k among the n values
+ * in(clamp(x+dx, 0, w-1), clamp(y+dy, 0, h-1)) for (dx, dy) in a convex kernel K
+ * (Sec. 3.1 pivot/count principle; Eq. 1-3 region membership; Sec. 3.3 method summary).
+ * k = (n-1)/2 for the median. Border handling is clamp-to-edge. Output values are always
+ * input values, so results are bit-exact for every dtype.
+ *
+ * Conventions for every call below:
+ *   - Image pointers are DEVICE pointers unless the name says "host". The caller owns them.
+ *     Rows are `pitch_bytes` apart; the same pitch applies to input and output. The
+ *     pitch must be at least w * element size and a multiple of the element size.
+ *     Input and output must not overlap (FIM_ERR_INVALID_ARG).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Filter calls are asynchronous on it. Argument errors return synchronously;
+ *     errors detected on the device are recorded in a status word that
+ *     fim_sync_status() reads.
+ *   - Float data is ordered by IEEE 754 totalOrder (-0 < +0). NaN inputs are ordered by
+ *     their bit patterns under the same total order; the filter does no arithmetic on
+ *     values, so denormals are never flushed.
+ *   - Kernel handles are host objects owned by the caller (fim_destroy_kernel).
+ *   - All entry points are thread-safe with respect to distinct handles.
+ */
+#ifndef FIM_H_
+#define FIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { FIM_U8 = 0, FIM_U16 = 1, FIM_F32 = 2 } fim_dtype;
+
+typedef enum { FIM_BORDER_CLAMP = 0 } fim_border;
+
+typedef enum {
+    FIM_OK = 0,
+    FIM_ERR_INVALID_ARG = 1, /* bad pointer, size, pitch, overlap or kernel shape */
+    FIM_ERR_UNSUPPORTED = 2, /* valid request this build cannot serve (e.g. kernel too large) */
+    FIM_ERR_OOM = 3,         /* device or host allocation failed */
+    FIM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    FIM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (persistent batch queue) */
+    FIM_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} fim_status;
+
+typedef struct fim_kernel fim_kernel;
+
+/* Largest kernel extent along x or y (max - min + 1) this build accepts. */
+#define FIM_MAX_KERNEL_EXTENT 257
+
+/*
+ * Disk kernel, Eq. 3 on the integer lattice: K = {(dx, dy) : dx^2 + dy^2 <= radius^2}.
+ * radius in [0, 128]. *out receives a new handle.
+ */
+fim_status fim_create_kernel_circle(int radius, fim_kernel** out);
+
+/*
+ * Disk kernel with an explicit bound: K = {(dx, dy) : dx^2 + dy^2 <= limit}, limit >= 0
+ * and floor(sqrt(limit)) <= 128. limit = r*r + r gives the fuller disk whose tap counts
+ * match Fig. 3b and Fig. 10 of the paper (21 taps at r = 2).
+ */
+fim_status fim_create_kernel_disk_limit(int64_t limit, fim_kernel** out);
+
+/*
+ * Axis-aligned ellipse with semi-axes a (along x) and b (along y), both in [0, 128]:
+ * K = {(dx, dy) : dx^2 b^2 + dy^2 a^2 <= a^2 b^2}, tested exactly in integers.
+ */
+fim_status fim_create_kernel_ellipse(int a, int b, fim_kernel** out);
+
+/*
+ * Convex polygon kernel (Sec. 6.2.3: a polygon replaces the circle test of Eq. 3).
+ * xy holds nverts (x, y) pairs, counter-clockwise, in pixel units relative to the output
+ * pixel; K is every lattice point inside or on the polygon (edge tolerance 1e-9).
+ * Returns FIM_ERR_INVALID_ARG when the polygon is not convex and counter-clockwise or
+ * holds no lattice point.
+ */
+fim_status fim_create_kernel_polygon(const double* xy, int nverts, fim_kernel** out);
+
+/*
+ * Kernel given by row spans: row dy0 + i covers dx in [lo[i], hi[i]], i < rows.
+ * Every row must be non-empty and the shape must be convex along columns too (each column
+ * a single run), else FIM_ERR_INVALID_ARG.
+ */
+fim_status fim_create_kernel_spans(const int* lo, const int* hi, int dy0, int rows, fim_kernel** out);
+
+/* Tap count n and bounding box of a kernel. Any output pointer may be NULL. */
+fim_status fim_kernel_info(const fim_kernel* k, int* ntaps, int* xmin, int* xmax, int* ymin, int* ymax);
+
+/* Frees a handle (NULL is ignored). The caller must not destroy a kernel still in use by a
+ * filter call that has not finished on its stream. */
+void fim_destroy_kernel(fim_kernel* k);
+
+/*
+ * Median filter (Sec. 3.3 steps 1-7). in/out: device images of w x h elements of `dtype`,
+ * rows pitch_bytes apart. w, h >= 1. Asynchronous on `stream`.
+ */
+fim_status fim_median(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                      const fim_kernel* k, fim_border border, void* stream);
+
+/*
+ * Percentile (rank-order) filter: the same method with target rank
+ * rank = round(percentile / 100 * (n - 1)) instead of (n - 1) / 2 (Sec. 6.2.5, Fig. 12-14).
+ * percentile in [0, 100].
+ */
+fim_status fim_percentile(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                          const fim_kernel* k, double percentile, fim_border border, void* stream);
+
+/*
+ * fim_median with HOST buffers: copies the input to the device, filters, copies the result
+ * back, and returns when the output is in `out_host`. Device buffers are allocated on
+ * first use and cached per thread. Rows are pitch_bytes apart in both host buffers.
+ */
+fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, size_t pitch_bytes,
+                           fim_dtype dtype, const fim_kernel* k, fim_border border, void* stream);
+
+/*
+ * Waits for `stream`, then returns and clears the device status word: FIM_OK, or the
+ * first device-side error recorded since the last call (FIM_ERR_TIMEOUT, FIM_ERR_INTERNAL).
+ */
+fim_status fim_sync_status(void* stream);
+
+/* Static, human-readable name of a status code. */
+const char* fim_status_string(fim_status s);
+
+/* Version of this library as "major.minor.patch". */
+const char* fim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIM_H_ */

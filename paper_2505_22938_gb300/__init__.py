@@ -1,0 +1,229 @@
+"""Thin Python binding of libfim, the GB300 exact isotropic median filter.
+
+Every function here marshals arguments into the C ABI declared in ``include/fim.h``
+and calls it; all filtering happens in the library's CUDA kernels. Names follow the C ABI.
+PyTorch is used only to hand over device pointers and streams (``tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``); the C signatures carry plain pointers.
+
+The library is built in-tree (``paper_2505_22938_gb300/_build/libfim.so``). Importing
+this module never falls back to any other implementation: if the library cannot be
+loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+FIM_U8, FIM_U16, FIM_F32 = 0, 1, 2
+FIM_BORDER_CLAMP = 0
+STATUS = {0: "FIM_OK", 1: "FIM_ERR_INVALID_ARG", 2: "FIM_ERR_UNSUPPORTED", 3: "FIM_ERR_OOM",
+          4: "FIM_ERR_CUDA", 5: "FIM_ERR_TIMEOUT", 6: "FIM_ERR_INTERNAL"}
+DTYPES = {"u8": FIM_U8, "u16": FIM_U16, "f32": FIM_F32}
+ELEM_SIZE = {FIM_U8: 1, FIM_U16: 2, FIM_F32: 4}
+
+# Every symbol include/fim.h declares, with (restype, argtypes).
+_c = ctypes
+_P = _c.c_void_p
+_PP = _c.POINTER(_c.c_void_p)
+SIGNATURES = {
+    "fim_create_kernel_circle": (_c.c_int, [_c.c_int, _PP]),
+    "fim_create_kernel_disk_limit": (_c.c_int, [_c.c_int64, _PP]),
+    "fim_create_kernel_ellipse": (_c.c_int, [_c.c_int, _c.c_int, _PP]),
+    "fim_create_kernel_polygon": (_c.c_int, [_P, _c.c_int, _PP]),
+    "fim_create_kernel_spans": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _PP]),
+    "fim_kernel_info": (_c.c_int, [_P, _P, _P, _P, _P, _P]),
+    "fim_destroy_kernel": (None, [_P]),
+    "fim_median": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
+    "fim_percentile": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_double,
+                                  _c.c_int, _P]),
+    "fim_median_host": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
+    "fim_sync_status": (_c.c_int, [_P]),
+    "fim_status_string": (_c.c_char_p, [_c.c_int]),
+    "fim_version": (_c.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FimError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libfim (building it first if needed) and declares every exported signature."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfim is not built ({path}); run paper_2505_22938_gb300.build.build()")
+            handle = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def _check(code: int, what: str) -> None:
+    if code != 0:
+        raise FimError(code, what)
+
+
+class Kernel:
+    """Owns a fim_kernel handle."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    @property
+    def info(self) -> dict:
+        vals = [ctypes.c_int() for _ in range(5)]
+        _check(lib().fim_kernel_info(self.handle, *[ctypes.byref(v) for v in vals]), "fim_kernel_info")
+        n, xmin, xmax, ymin, ymax = (v.value for v in vals)
+        return dict(ntaps=n, xmin=xmin, xmax=xmax, ymin=ymin, ymax=ymax)
+
+    def close(self) -> None:
+        if self.handle:
+            lib().fim_destroy_kernel(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _new_kernel(fn_name: str, *args) -> Kernel:
+    h = ctypes.c_void_p()
+    _check(getattr(lib(), fn_name)(*args, ctypes.byref(h)), fn_name)
+    return Kernel(h)
+
+
+def fim_create_kernel_circle(radius: int) -> Kernel:
+    return _new_kernel("fim_create_kernel_circle", int(radius))
+
+
+def fim_create_kernel_disk_limit(limit: int) -> Kernel:
+    return _new_kernel("fim_create_kernel_disk_limit", int(limit))
+
+
+def fim_create_kernel_ellipse(a: int, b: int) -> Kernel:
+    return _new_kernel("fim_create_kernel_ellipse", int(a), int(b))
+
+
+def fim_create_kernel_polygon(xy) -> Kernel:
+    flat = [float(v) for p in xy for v in p]
+    arr = (ctypes.c_double * len(flat))(*flat)
+    return _new_kernel("fim_create_kernel_polygon", ctypes.cast(arr, ctypes.c_void_p), len(flat) // 2)
+
+
+def fim_create_kernel_spans(lo, hi, dy0: int) -> Kernel:
+    lo = [int(v) for v in lo]
+    hi = [int(v) for v in hi]
+    a = (ctypes.c_int * len(lo))(*lo)
+    b = (ctypes.c_int * len(hi))(*hi)
+    return _new_kernel("fim_create_kernel_spans", ctypes.cast(a, ctypes.c_void_p), ctypes.cast(b, ctypes.c_void_p),
+                       int(dy0), len(lo))
+
+
+def fim_median(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+               stream: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
+    """Raw C-ABI call on device pointers (asynchronous on `stream`)."""
+    _check(lib().fim_median(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, border, stream or None),
+           "fim_median")
+
+
+def fim_percentile(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+                   percentile: float, stream: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
+    _check(lib().fim_percentile(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, float(percentile),
+                                border, stream or None), "fim_percentile")
+
+
+def fim_median_host(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+                    stream: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
+    """Raw C-ABI call on HOST pointers; returns once the result is in host memory."""
+    _check(lib().fim_median_host(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, border,
+                                 stream or None), "fim_median_host")
+
+
+def fim_sync_status(stream: int = 0) -> int:
+    return int(lib().fim_sync_status(stream or None))
+
+
+def fim_status_string(code: int) -> str:
+    return lib().fim_status_string(int(code)).decode()
+
+
+def fim_version() -> str:
+    return lib().fim_version().decode()
+
+
+# ---------------------------------------------------------------------------------------------
+# torch conveniences (device memory and streams only)
+# ---------------------------------------------------------------------------------------------
+
+def _torch_dtype_code(t) -> int:
+    import torch
+    m = {torch.uint8: FIM_U8, torch.uint16: FIM_U16, torch.float32: FIM_F32}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def median(img, kernel: Kernel, out=None, stream=None):
+    """Median-filters a 2-D CUDA tensor (uint8, uint16 or float32) on the current stream."""
+    import torch
+    assert img.is_cuda and img.dim() == 2 and img.stride(1) == 1
+    code = _torch_dtype_code(img)
+    if out is None:
+        out = torch.empty_like(img, memory_format=torch.contiguous_format)
+    assert out.shape == img.shape and out.dtype == img.dtype and out.stride(0) == img.stride(0)
+    pitch = img.stride(0) * img.element_size()
+    h, w = img.shape
+    fim_median(img.data_ptr(), out.data_ptr(), w, h, pitch, code, kernel, _stream_handle(stream))
+    return out
+
+
+def percentile(img, kernel: Kernel, pct: float, out=None, stream=None):
+    import torch
+    assert img.is_cuda and img.dim() == 2 and img.stride(1) == 1
+    code = _torch_dtype_code(img)
+    if out is None:
+        out = torch.empty_like(img, memory_format=torch.contiguous_format)
+    pitch = img.stride(0) * img.element_size()
+    h, w = img.shape
+    fim_percentile(img.data_ptr(), out.data_ptr(), w, h, pitch, code, kernel, pct, _stream_handle(stream))
+    return out
+
+
+def median_host(arr, kernel: Kernel, out=None, stream=None):
+    """Median-filters a 2-D host numpy array through fim_median_host (copies in and out)."""
+    import numpy as np
+    codes = {np.dtype(np.uint8): FIM_U8, np.dtype(np.uint16): FIM_U16, np.dtype(np.float32): FIM_F32}
+    a = np.ascontiguousarray(arr)
+    code = codes[a.dtype]
+    if out is None:
+        out = np.empty_like(a)
+    h, w = a.shape
+    fim_median_host(a.ctypes.data, out.ctypes.data, w, h, a.strides[0], code, kernel,
+                    _stream_handle(stream) if stream is not None else 0)
+    return out

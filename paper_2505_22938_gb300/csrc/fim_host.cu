@@ -1,0 +1,447 @@
+// Host side of libfim: kernel shapes, tile planning, argument checks and the C ABI.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+
+#include "fim_internal.h"
+
+namespace fim {
+namespace {
+
+int64_t isqrt64(int64_t v) {
+    if (v <= 0) return 0;
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+// Fills the column runs from the row spans; fails unless every column is a single run and
+// every row is non-empty (the shape is convex along both axes).
+fim_status finish_kernel(fim_kernel* k) {
+    const int rows = (int)k->rlo.size();
+    if (rows <= 0) return FIM_ERR_INVALID_ARG;
+    int xmin = k->rlo[0], xmax = k->rhi[0];
+    int64_t n = 0;
+    for (int i = 0; i < rows; ++i) {
+        if (k->rlo[i] > k->rhi[i]) return FIM_ERR_INVALID_ARG;
+        xmin = std::min(xmin, k->rlo[i]);
+        xmax = std::max(xmax, k->rhi[i]);
+        n += k->rhi[i] - k->rlo[i] + 1;
+    }
+    k->xmin = xmin;
+    k->xmax = xmax;
+    k->ymax = k->ymin + rows - 1;
+    if (xmax - xmin + 1 > FIM_MAX_KERNEL_EXTENT || rows > FIM_MAX_KERNEL_EXTENT) return FIM_ERR_UNSUPPORTED;
+    const int cols = xmax - xmin + 1;
+    k->ctop.assign(cols, 0);
+    k->cbot.assign(cols, 0);
+    for (int j = 0; j < cols; ++j) {
+        const int dx = xmin + j;
+        int first = -1, last = -1;
+        for (int i = 0; i < rows; ++i) {
+            const bool in = k->rlo[i] <= dx && dx <= k->rhi[i];
+            if (in) {
+                if (first < 0) first = i;
+                else if (last != i - 1) return FIM_ERR_INVALID_ARG;  // second run in this column
+                last = i;
+            }
+        }
+        if (first < 0) return FIM_ERR_INVALID_ARG;  // empty column inside the bounding box
+        k->ctop[j] = k->ymin + first;
+        k->cbot[j] = k->ymin + last;
+    }
+    k->n = (int)n;
+    return FIM_OK;
+}
+
+fim_status new_kernel(fim_kernel** out, fim_kernel** k) {
+    if (!out) return FIM_ERR_INVALID_ARG;
+    *out = nullptr;
+    *k = new (std::nothrow) fim_kernel();
+    return *k ? FIM_OK : FIM_ERR_OOM;
+}
+
+fim_status publish(fim_kernel* k, fim_kernel** out) {
+    fim_status s = finish_kernel(k);
+    if (s != FIM_OK) {
+        delete k;
+        return s;
+    }
+    *out = k;
+    return FIM_OK;
+}
+
+fim_status disk_kernel(int64_t limit, fim_kernel** out) {
+    fim_kernel* k;
+    fim_status s = new_kernel(out, &k);
+    if (s != FIM_OK) return s;
+    const int r = (int)isqrt64(limit);
+    k->shape = kShapeDisk;
+    k->r2 = limit;
+    k->ymin = -r;
+    for (int dy = -r; dy <= r; ++dy) {
+        const int half = (int)isqrt64(limit - (int64_t)dy * dy);
+        k->rlo.push_back(-half);
+        k->rhi.push_back(half);
+    }
+    return publish(k, out);
+}
+
+}  // namespace
+
+int device_smem_limit() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+static int elem_size(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); }
+
+fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, Plan* p) {
+    memset(p, 0, sizeof(*p));
+    p->dtype = dtype;
+    p->w = w;
+    p->h = h;
+    p->T = ts.T;
+    p->RB = ts.RB;
+    p->G = ts.G;
+    p->threads = 2 * ts.T * ts.RB;
+    p->nwarps = p->threads / 32;
+    p->shape = k->shape;
+    p->r2 = (int)k->r2;
+    p->xmin = k->xmin;
+    p->xmax = k->xmax;
+    p->ymin = k->ymin;
+    p->ymax = k->ymax;
+    p->nrows = k->ymax - k->ymin + 1;
+    p->ncols = k->xmax - k->xmin + 1;
+    p->n = k->n;
+    p->rank = rank;
+    p->S = ts.T + (k->xmax - k->xmin);
+    p->SH = ts.T + (k->ymax - k->ymin);
+    if (p->S > 256 || p->SH > 256 || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
+    p->tiles_x = (w + ts.T - 1) / ts.T;
+    p->tiles_y = (h + ts.T - 1) / ts.T;
+    const int T = ts.T, S = p->S;
+    // Footprint: the union of the kernel over the tile's output pixels, row by row (Fig. 10).
+    int64_t N = 0;
+    for (int v = 0; v < p->SH; ++v) {
+        const int i0 = std::max(0, v - T + 1), i1 = std::min(p->nrows - 1, v);
+        int lo = 1 << 30, hi = -(1 << 30);
+        for (int i = i0; i <= i1; ++i) {
+            lo = std::min(lo, k->rlo[i]);
+            hi = std::max(hi, k->rhi[i]);
+        }
+        p->fl[v] = (int16_t)(lo - k->xmin);
+        p->fr[v] = (int16_t)(T - 1 + hi - k->xmin);
+        N += p->fr[v] - p->fl[v] + 1;
+    }
+    if (N > 65536) return FIM_ERR_UNSUPPORTED;
+    p->N = (int)N;
+    p->cx0 = S / 2;
+    p->cy0 = p->SH / 2;
+    p->div_magic = (unsigned)(((1ull << 32) + (unsigned)S - 1) / (unsigned)S);
+    int hs = 0;
+    while (((p->N - 1) >> hs) >= kSeedBins) ++hs;
+    p->hist_shift = hs;
+    for (int j = 0; j < p->ncols; ++j) {
+        const int dx = k->xmin + j;
+        p->vA[j] = k->ctop[j] * S + dx;
+        p->vB[j] = (k->cbot[j] + 1) * S + dx;
+    }
+    for (int i = 0; i < p->nrows; ++i) {
+        const int dy = k->ymin + i;
+        p->hL[i] = dy * S + k->rlo[i];
+        p->hH[i] = dy * S + k->rhi[i] + 1;
+        p->spans[i] = (int)((uint32_t)(k->rlo[i] & 0xffff) | ((uint32_t)k->rhi[i] << 16));
+    }
+    // Shared memory: [keys | ordinal image] [A] [B] [histograms | medians + seed histograms] [spans]
+    const size_t area = (size_t)S * p->SH;
+    const size_t keyb = (size_t)elem_size(dtype);
+    size_t off = 0;
+    p->off_keys = (int)off;
+    off += align16(area * std::max<size_t>(keyb, 2));
+    p->off_a = (int)off;
+    off += align16((size_t)p->N * 2);
+    p->off_b = (int)off;
+    off += align16((size_t)p->N * 2);
+    p->off_h = (int)off;
+    const size_t hsort = (size_t)kSortBins * p->nwarps * 4;
+    const size_t hsolve = align16((size_t)T * T * 2) + (size_t)kSeedBins * p->nwarps * 4;
+    off += align16(std::max(hsort, hsolve));
+    p->off_spans = (int)off;
+    off += align16((size_t)p->nrows * 4);
+    if (off > (size_t)1 << 30) return FIM_ERR_UNSUPPORTED;
+    p->smem_bytes = (int)off;
+    return FIM_OK;
+}
+
+fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts) {
+    static const TileShape cands[] = {{64, 8, 4}, {32, 8, 4}};
+    for (const TileShape& c : cands) {
+        Plan* p = new (std::nothrow) Plan;
+        if (!p) return FIM_ERR_OOM;
+        fim_status s = make_plan(k, dtype, 0, 1, 1, c, p);
+        const int bytes = p->smem_bytes;
+        delete p;
+        if (s == FIM_OK && bytes <= smem_limit) {
+            *ts = c;
+            return FIM_OK;
+        }
+    }
+    return FIM_ERR_UNSUPPORTED;
+}
+
+}  // namespace fim
+
+using namespace fim;
+
+namespace {
+
+struct Hostbufs {
+    void* d_in = nullptr;
+    void* d_out = nullptr;
+    size_t bytes = 0;
+    ~Hostbufs() {
+        if (d_in) cudaFree(d_in);
+        if (d_out) cudaFree(d_out);
+    }
+};
+
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + bytes && pb < pa + bytes;
+}
+
+fim_status check_image_args(const void* in, const void* out, int w, int h, size_t pitch, int dtype,
+                            const fim_kernel* k, int border) {
+    if (!in || !out || !k || w <= 0 || h <= 0) return FIM_ERR_INVALID_ARG;
+    if (dtype != FIM_U8 && dtype != FIM_U16 && dtype != FIM_F32) return FIM_ERR_INVALID_ARG;
+    if (border != FIM_BORDER_CLAMP) return FIM_ERR_INVALID_ARG;
+    const size_t es = (size_t)elem_size(dtype);
+    if (pitch < (size_t)w * es || pitch % es != 0) return FIM_ERR_INVALID_ARG;
+    const size_t span = pitch * (size_t)(h - 1) + (size_t)w * es;
+    if (ranges_overlap(in, out, span)) return FIM_ERR_INVALID_ARG;
+    return FIM_OK;
+}
+
+fim_status filter_rank(const void* in, void* out, int w, int h, size_t pitch, int dtype, const fim_kernel* k,
+                       int rank, cudaStream_t stream) {
+    static thread_local int smem_limit = -1;
+    if (smem_limit < 0) smem_limit = device_smem_limit();
+    if (smem_limit <= 0) return FIM_ERR_CUDA;
+    TileShape ts;
+    fim_status s = choose_tile(k, dtype, smem_limit, &ts);
+    if (s != FIM_OK) return s;
+    Plan* p = new (std::nothrow) Plan;
+    if (!p) return FIM_ERR_OOM;
+    s = make_plan(k, dtype, rank, w, h, ts, p);
+    if (s == FIM_OK) {
+        p->in = in;
+        p->out = out;
+        p->pitch = (long long)pitch;
+        s = launch_tile_kernel(*p, stream);
+    }
+    delete p;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+fim_status fim_create_kernel_circle(int radius, fim_kernel** out) {
+    if (!out || radius < 0 || radius > 128) return FIM_ERR_INVALID_ARG;
+    return disk_kernel((int64_t)radius * radius, out);
+}
+
+fim_status fim_create_kernel_disk_limit(int64_t limit, fim_kernel** out) {
+    if (!out || limit < 0 || isqrt64(limit) > 128) return FIM_ERR_INVALID_ARG;
+    return disk_kernel(limit, out);
+}
+
+fim_status fim_create_kernel_ellipse(int a, int b, fim_kernel** out) {
+    if (!out || a < 0 || b < 0 || a > 128 || b > 128) return FIM_ERR_INVALID_ARG;
+    fim_kernel* k;
+    fim_status s = new_kernel(out, &k);
+    if (s != FIM_OK) return s;
+    k->shape = kShapeSpans;
+    k->r2 = 0;
+    const int64_t A = a, B = b;
+    if (b == 0) {
+        k->ymin = 0;
+        k->rlo.push_back(-a);
+        k->rhi.push_back(a);
+    } else {
+        k->ymin = -b;
+        for (int dy = -b; dy <= b; ++dy) {
+            const int64_t rest = A * A * B * B - (int64_t)dy * dy * A * A;  // >= 0
+            const int half = (int)isqrt64(rest / (B * B));
+            k->rlo.push_back(-half);
+            k->rhi.push_back(half);
+        }
+    }
+    return publish(k, out);
+}
+
+fim_status fim_create_kernel_polygon(const double* xy, int nverts, fim_kernel** out) {
+    if (!out || !xy || nverts < 3 || nverts > 4096) return FIM_ERR_INVALID_ARG;
+    const double eps = 1e-9;
+    double area2 = 0.0;
+    double xlo = xy[0], xhi = xy[0], ylo = xy[1], yhi = xy[1];
+    for (int i = 0; i < nverts; ++i) {
+        const double ax = xy[2 * i], ay = xy[2 * i + 1];
+        const double bx = xy[2 * ((i + 1) % nverts)], by = xy[2 * ((i + 1) % nverts) + 1];
+        const double cx = xy[2 * ((i + 2) % nverts)], cy = xy[2 * ((i + 2) % nverts) + 1];
+        if (!isfinite(ax) || !isfinite(ay)) return FIM_ERR_INVALID_ARG;
+        area2 += ax * by - bx * ay;
+        if ((bx - ax) * (cy - by) - (by - ay) * (cx - bx) < -eps) return FIM_ERR_INVALID_ARG;  // reflex turn
+        xlo = std::min(xlo, ax);
+        xhi = std::max(xhi, ax);
+        ylo = std::min(ylo, ay);
+        yhi = std::max(yhi, ay);
+    }
+    if (area2 <= 0.0) return FIM_ERR_INVALID_ARG;
+    if (xhi - xlo > 2.0 * FIM_MAX_KERNEL_EXTENT || yhi - ylo > 2.0 * FIM_MAX_KERNEL_EXTENT) return FIM_ERR_UNSUPPORTED;
+    fim_kernel* k;
+    fim_status s = new_kernel(out, &k);
+    if (s != FIM_OK) return s;
+    k->shape = kShapeSpans;
+    k->r2 = 0;
+    const int x0 = (int)floor(xlo) - 1, x1 = (int)ceil(xhi) + 1;
+    const int y0 = (int)floor(ylo) - 1, y1 = (int)ceil(yhi) + 1;
+    bool started = false;
+    for (int dy = y0; dy <= y1; ++dy) {
+        int lo = 1 << 30, hi = -(1 << 30);
+        for (int dx = x0; dx <= x1; ++dx) {
+            bool inside = true;
+            for (int i = 0; i < nverts && inside; ++i) {
+                const double ax = xy[2 * i], ay = xy[2 * i + 1];
+                const double bx = xy[2 * ((i + 1) % nverts)], by = xy[2 * ((i + 1) % nverts) + 1];
+                inside = (bx - ax) * (dy - ay) - (by - ay) * (dx - ax) >= -eps;
+            }
+            if (inside) {
+                lo = std::min(lo, dx);
+                hi = std::max(hi, dx);
+            }
+        }
+        if (lo <= hi) {
+            if (!started) {
+                k->ymin = dy;
+                started = true;
+            }
+            k->rlo.push_back(lo);
+            k->rhi.push_back(hi);
+        } else if (started) {
+            break;
+        }
+    }
+    if (!started) {
+        delete k;
+        return FIM_ERR_INVALID_ARG;
+    }
+    return publish(k, out);
+}
+
+fim_status fim_create_kernel_spans(const int* lo, const int* hi, int dy0, int rows, fim_kernel** out) {
+    if (!out || !lo || !hi || rows <= 0 || rows > FIM_MAX_KERNEL_EXTENT) return FIM_ERR_INVALID_ARG;
+    if (dy0 < -4 * FIM_MAX_KERNEL_EXTENT || dy0 > 4 * FIM_MAX_KERNEL_EXTENT) return FIM_ERR_INVALID_ARG;
+    for (int i = 0; i < rows; ++i)
+        if (lo[i] < -4 * FIM_MAX_KERNEL_EXTENT || hi[i] > 4 * FIM_MAX_KERNEL_EXTENT) return FIM_ERR_INVALID_ARG;
+    fim_kernel* k;
+    fim_status s = new_kernel(out, &k);
+    if (s != FIM_OK) return s;
+    k->shape = kShapeSpans;
+    k->r2 = 0;
+    k->ymin = dy0;
+    k->rlo.assign(lo, lo + rows);
+    k->rhi.assign(hi, hi + rows);
+    return publish(k, out);
+}
+
+fim_status fim_kernel_info(const fim_kernel* k, int* ntaps, int* xmin, int* xmax, int* ymin, int* ymax) {
+    if (!k) return FIM_ERR_INVALID_ARG;
+    if (ntaps) *ntaps = k->n;
+    if (xmin) *xmin = k->xmin;
+    if (xmax) *xmax = k->xmax;
+    if (ymin) *ymin = k->ymin;
+    if (ymax) *ymax = k->ymax;
+    return FIM_OK;
+}
+
+void fim_destroy_kernel(fim_kernel* k) { delete k; }
+
+fim_status fim_median(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                      const fim_kernel* k, fim_border border, void* stream) {
+    fim_status s = check_image_args(in, out, w, h, pitch_bytes, dtype, k, border);
+    if (s != FIM_OK) return s;
+    return filter_rank(in, out, w, h, pitch_bytes, dtype, k, (k->n - 1) / 2, (cudaStream_t)stream);
+}
+
+fim_status fim_percentile(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                          const fim_kernel* k, double percentile, fim_border border, void* stream) {
+    fim_status s = check_image_args(in, out, w, h, pitch_bytes, dtype, k, border);
+    if (s != FIM_OK) return s;
+    if (!(percentile >= 0.0 && percentile <= 100.0)) return FIM_ERR_INVALID_ARG;
+    const int rank = (int)floor(percentile / 100.0 * (k->n - 1) + 0.5);
+    return filter_rank(in, out, w, h, pitch_bytes, dtype, k, std::min(std::max(rank, 0), k->n - 1),
+                       (cudaStream_t)stream);
+}
+
+fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, size_t pitch_bytes,
+                           fim_dtype dtype, const fim_kernel* k, fim_border border, void* stream) {
+    fim_status s = check_image_args(in_host, out_host, w, h, pitch_bytes, dtype, k, border);
+    if (s != FIM_OK) return s;
+    static thread_local Hostbufs bufs;
+    const size_t es = (size_t)elem_size(dtype);
+    const size_t dpitch = (size_t)w * es;
+    const size_t bytes = dpitch * (size_t)h;
+    if (bufs.bytes < bytes) {
+        if (bufs.d_in) cudaFree(bufs.d_in);
+        if (bufs.d_out) cudaFree(bufs.d_out);
+        bufs.d_in = bufs.d_out = nullptr;
+        bufs.bytes = 0;
+        if (cudaMalloc(&bufs.d_in, bytes) != cudaSuccess || cudaMalloc(&bufs.d_out, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return FIM_ERR_OOM;
+        }
+        bufs.bytes = bytes;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpy2DAsync(bufs.d_in, dpitch, in_host, pitch_bytes, dpitch, h, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return FIM_ERR_CUDA;
+    s = filter_rank(bufs.d_in, bufs.d_out, w, h, dpitch, dtype, k, (k->n - 1) / 2, st);
+    if (s != FIM_OK) return s;
+    if (cudaMemcpy2DAsync(out_host, pitch_bytes, bufs.d_out, dpitch, dpitch, h, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return FIM_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FIM_ERR_CUDA;
+    return FIM_OK;
+}
+
+fim_status fim_sync_status(void* stream) { return read_and_clear_device_status((cudaStream_t)stream); }
+
+const char* fim_status_string(fim_status s) {
+    switch (s) {
+        case FIM_OK: return "FIM_OK";
+        case FIM_ERR_INVALID_ARG: return "FIM_ERR_INVALID_ARG";
+        case FIM_ERR_UNSUPPORTED: return "FIM_ERR_UNSUPPORTED";
+        case FIM_ERR_OOM: return "FIM_ERR_OOM";
+        case FIM_ERR_CUDA: return "FIM_ERR_CUDA";
+        case FIM_ERR_TIMEOUT: return "FIM_ERR_TIMEOUT";
+        case FIM_ERR_INTERNAL: return "FIM_ERR_INTERNAL";
+    }
+    return "FIM_ERR_UNKNOWN";
+}
+
+const char* fim_version(void) { return "0.1.0"; }
+
+}  // extern "C"

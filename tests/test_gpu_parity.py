@@ -1,0 +1,144 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Sizes span several tiles and ragged edges; kernels cover disks at every workload radius
+that fits the oracle's time, the workload hexagon and ellipse, asymmetric and even-n span
+kernels, and the degenerate cases (1x1, one row, one column, radius 0, constant images,
+the adversarial checkerboard). The tolerance is 0: the output is a selected input value.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from helpers import assert_bit_exact, fim_kernel, gpu_filter, oracle_offsets
+
+pytestmark = pytest.mark.gpu
+
+NP = {"u8": np.uint8, "u16": np.uint16, "f32": np.float32}
+
+
+def run_case(img, kind, *args, pitch_elems=None, percentile=None):
+    k = fim_kernel(kind, *args)
+    off = oracle_offsets(kind, *args)
+    assert k.info["ntaps"] == len(off)
+    rank = None if percentile is None else oracle.percentile_rank(len(off), percentile)
+    got = gpu_filter(img, k, pitch_elems=pitch_elems, percentile=percentile)
+    exp = oracle.median_filter(img, off, rank=rank)
+    assert_bit_exact(got, exp, f"{kind}{args} {img.dtype} {img.shape}")
+
+
+def test_config1_full():
+    """u8 256x256 uniform, disk r=4 (49 taps), whole image."""
+    run_case(datagen.config1_image(), "circle", 4)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 8, 16, 32, 48])
+def test_u16_photo_crops(r):
+    img = datagen.config2_image(4096, 4096)[1000:1000 + 203, 2000:2000 + 217]
+    run_case(np.ascontiguousarray(img), "circle", r)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+@pytest.mark.parametrize("r", [5, 21])
+def test_dtypes_ragged(dtype, r):
+    img = datagen.image_for(dtype, 100 + r, 141, 167)
+    run_case(img, "circle", r)
+
+
+@pytest.mark.parametrize("r", [24, 40, 64])
+def test_f32_disks(r):
+    img = datagen.image_for("f32", 300 + r, 120, 133)
+    run_case(img, "circle", r)
+
+
+def test_f32_hexagon64():
+    img = datagen.image_for("f32", 401, 96, 101)
+    run_case(img, "polygon", oracle.regular_polygon_vertices(6, 64.0))
+
+
+def test_f32_ellipse80x40():
+    img = datagen.image_for("f32", 402, 90, 77)
+    run_case(img, "ellipse", 80, 40)
+
+
+@pytest.mark.parametrize("spec", [
+    ("spans", [0, -1, -2], [2, 1, 0], -2),            # asymmetric
+    ("spans", [0, 0], [1, 1], 0),                     # even n = 4, lower median
+    ("spans", [-3], [2], 0),                          # one row
+    ("spans", [0] * 7, [0] * 7, -3),                  # one column
+    ("spans", [-1] * 3, [1] * 3, -1),                 # 3x3 square
+    ("ellipse", 9, 3),
+    ("disk_limit", 48 * 48 + 48),                     # the fuller disk of Fig. 10
+])
+def test_kernel_shapes(spec):
+    img = datagen.image_for("u16", 77, 97, 131)
+    run_case(img, *spec)
+
+
+@pytest.mark.parametrize("sides,R,phase", [(4, 12.0, 45.0), (8, 15.5, 10.0), (12, 30.0, 0.0), (3, 20.0, 90.0)])
+def test_polygons(sides, R, phase):
+    img = datagen.image_for("u8", 88, 90, 111)
+    run_case(img, "polygon", oracle.regular_polygon_vertices(sides, R, phase))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 75), (66, 1), (2, 3), (31, 33), (64, 64), (65, 129)])
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_degenerate_sizes(shape, dtype):
+    img = datagen.image_for(dtype, 55, *shape)
+    run_case(img, "circle", 6)
+
+
+def test_radius0_identity_and_constant():
+    img = datagen.image_for("u16", 9, 70, 90)
+    run_case(img, "circle", 0)
+    run_case(np.full((70, 90), 1234, np.uint16), "circle", 20)
+    run_case(np.full((50, 40), -2.5, np.float32), "ellipse", 30, 10)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_adversarial_checkerboard(dtype):
+    img = datagen.adversarial_tile(150, 170, dtype, border=24)
+    run_case(img, "circle", 20)
+
+
+def test_pitch_wider_than_row():
+    img = datagen.image_for("u16", 12, 77, 101)
+    run_case(img, "circle", 9, pitch_elems=128)
+    img = datagen.image_for("f32", 13, 50, 61)
+    run_case(img, "circle", 7, pitch_elems=64)
+
+
+@pytest.mark.parametrize("pct", [0, 10, 30, 50, 70, 90, 100])
+def test_percentiles(pct):
+    img = datagen.image_for("u16", 61, 120, 99)
+    run_case(img, "circle", 12, percentile=pct)
+
+
+def test_float_signed_zero_and_denormals():
+    rng = np.random.default_rng(5)
+    vals = np.array([0.0, -0.0, 1e-45, -1e-45, 2e-40, -2e-40, 1.0, -1.0, 3e38, -3e38], np.float32)
+    img = vals[rng.integers(0, len(vals), size=(60, 70))]
+    run_case(img, "circle", 3)
+    run_case(img, "circle", 11)
+
+
+def test_full_size_config2_sampled():
+    """4096x4096 u16 at r = 8, 32, 48 in the launch configuration the bench times: every
+    tile-border row/column sample plus random pixels against the oracle, point by point."""
+    import torch
+    import paper_2505_22938_gb300 as fim
+    from helpers import to_device, to_host
+    img = datagen.config2_image()
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.integers(0, 4096, 3000), np.array([0, 4095, 63, 64, 127, 128, 4032, 4031])])
+    ys = np.concatenate([rng.integers(0, 4096, 3000), np.array([4095, 0, 64, 63, 128, 127, 4031, 4032])])
+    store, _ = to_device(img)
+    out = torch.empty_like(store)
+    for r in (8, 32, 48):
+        k = fim.fim_create_kernel_circle(r)
+        fim.median(store, k, out=out)
+        torch.cuda.synchronize()
+        assert fim.fim_sync_status() == 0
+        got = to_host(out)[ys, xs]
+        exp = oracle.median_points(img, oracle.disk_offsets(r), xs, ys)
+        assert np.array_equal(got, exp), f"r={r}: {np.sum(got != exp)} of {len(xs)} samples differ"
