@@ -123,11 +123,30 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
  */
 fim_status fim_sync_status(void* stream);
 
+/*
+ * Tiling the filter would use for this kernel, dtype and image size on the current device:
+ * output tile tile_w x tile_h, footprint pixels per tile, threads per CTA, dynamic shared
+ * memory per CTA. Any output pointer may be NULL. The environment variable
+ * FIM_TILE="tile_w,tile_h,bands,seeds" overrides the choice (tile_w a power of two and a
+ * multiple of 32; FIM_ERR_UNSUPPORTED if it does not fit the device).
+ */
+fim_status fim_plan_info(const fim_kernel* k, fim_dtype dtype, int w, int h, int* tile_w, int* tile_h,
+                         int* footprint, int* threads, int* smem_bytes);
+
 /* Static, human-readable name of a status code. */
 const char* fim_status_string(fim_status s);
 
 /* Version of this library as "major.minor.patch". */
 const char* fim_version(void);
+
+/*
+ * Diagnostics. Attaches a device buffer of tiles * 8 uint64 that every following filter
+ * launch (from any thread) fills with clock64() stamps at its phase boundaries: load, sort,
+ * structure build, seeds, seed rows, vertical sweeps, output, end; one row of 8 per tile
+ * index below `tiles`. fim_debug_phase_clocks(NULL, 0) detaches it. The buffer stays owned
+ * by the caller and must outlive the launches that use it.
+ */
+fim_status fim_debug_phase_clocks(void* dev_buf, int tiles);
 
 #ifdef __cplusplus
 }

@@ -43,6 +43,8 @@ SIGNATURES = {
     "fim_sync_status": (_c.c_int, [_P]),
     "fim_status_string": (_c.c_char_p, [_c.c_int]),
     "fim_version": (_c.c_char_p, []),
+    "fim_debug_phase_clocks": (_c.c_int, [_P, _c.c_int]),
+    "fim_plan_info": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -169,6 +171,16 @@ def fim_status_string(code: int) -> str:
 
 def fim_version() -> str:
     return lib().fim_version().decode()
+
+
+def fim_plan_info(kernel: Kernel, dtype: int, w: int, h: int) -> dict:
+    vals = [ctypes.c_int() for _ in range(5)]
+    _check(lib().fim_plan_info(kernel.handle, dtype, w, h, *[ctypes.byref(v) for v in vals]), "fim_plan_info")
+    return dict(zip(("tile_w", "tile_h", "footprint", "threads", "smem_bytes"), (v.value for v in vals)))
+
+
+def fim_debug_phase_clocks(dev_ptr: int, tiles: int) -> None:
+    _check(lib().fim_debug_phase_clocks(dev_ptr or None, int(tiles)), "fim_debug_phase_clocks")
 
 
 # ---------------------------------------------------------------------------------------------

@@ -1,5 +1,7 @@
 // Host side of libfim: kernel shapes, tile planning, argument checks and the C ABI.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -109,11 +111,18 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->dtype = dtype;
     p->w = w;
     p->h = h;
-    p->T = ts.T;
+    p->Tx = ts.Tx;
+    p->Ty = ts.Ty;
+    p->txshift = 0;
+    while ((1 << p->txshift) < ts.Tx) ++p->txshift;
+    if ((1 << p->txshift) != ts.Tx || ts.Tx % 32 != 0 || ts.Ty % ts.RB != 0 || ts.Tx % ts.G != 0 ||
+        ts.Ty / ts.RB < 2 || ts.Tx / ts.G < 2)
+        return FIM_ERR_INTERNAL;
     p->RB = ts.RB;
     p->G = ts.G;
-    p->threads = 2 * ts.T * ts.RB;
+    p->threads = 2 * ts.Tx * ts.RB;
     p->nwarps = p->threads / 32;
+    if (p->threads > 1024 || p->nwarps > 32) return FIM_ERR_INTERNAL;
     p->shape = k->shape;
     p->r2 = (int)k->r2;
     p->xmin = k->xmin;
@@ -124,26 +133,28 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->ncols = k->xmax - k->xmin + 1;
     p->n = k->n;
     p->rank = rank;
-    p->S = ts.T + (k->xmax - k->xmin);
-    p->SH = ts.T + (k->ymax - k->ymin);
+    p->S = ts.Tx + (k->xmax - k->xmin);
+    p->SH = ts.Ty + (k->ymax - k->ymin);
     if (p->S > 256 || p->SH > 256 || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
-    p->tiles_x = (w + ts.T - 1) / ts.T;
-    p->tiles_y = (h + ts.T - 1) / ts.T;
-    const int T = ts.T, S = p->S;
+    p->SP = (p->S + 1) & ~1;
+    if ((p->SP / 2) % 2 == 0) p->SP += 2;  // odd number of 32-bit words per row: no bank aliasing
+    p->tiles_x = (w + ts.Tx - 1) / ts.Tx;
+    p->tiles_y = (h + ts.Ty - 1) / ts.Ty;
+    const int Tx = ts.Tx, Ty = ts.Ty, S = p->S, SP = p->SP;
     // Footprint: the union of the kernel over the tile's output pixels, row by row (Fig. 10).
     int64_t N = 0;
     for (int v = 0; v < p->SH; ++v) {
-        const int i0 = std::max(0, v - T + 1), i1 = std::min(p->nrows - 1, v);
+        const int i0 = std::max(0, v - Ty + 1), i1 = std::min(p->nrows - 1, v);
         int lo = 1 << 30, hi = -(1 << 30);
         for (int i = i0; i <= i1; ++i) {
             lo = std::min(lo, k->rlo[i]);
             hi = std::max(hi, k->rhi[i]);
         }
-        p->fl[v] = (int16_t)(lo - k->xmin);
-        p->fr[v] = (int16_t)(T - 1 + hi - k->xmin);
-        N += p->fr[v] - p->fl[v] + 1;
+        const int fl = lo - k->xmin, fr = Tx - 1 + hi - k->xmin;
+        p->frow[v] = (int)((uint32_t)(fl & 0xffff) | ((uint32_t)fr << 16));
+        N += fr - fl + 1;
     }
-    if (N > 65536) return FIM_ERR_UNSUPPORTED;
+    if (N > 65535) return FIM_ERR_UNSUPPORTED;
     p->N = (int)N;
     p->cx0 = S / 2;
     p->cy0 = p->SH / 2;
@@ -153,39 +164,90 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->hist_shift = hs;
     for (int j = 0; j < p->ncols; ++j) {
         const int dx = k->xmin + j;
-        p->vA[j] = k->ctop[j] * S + dx;
-        p->vB[j] = (k->cbot[j] + 1) * S + dx;
+        p->vtab[2 * j] = k->ctop[j] * SP + dx;
+        p->vtab[2 * j + 1] = (k->cbot[j] + 1) * SP + dx;
     }
     for (int i = 0; i < p->nrows; ++i) {
         const int dy = k->ymin + i;
-        p->hL[i] = dy * S + k->rlo[i];
-        p->hH[i] = dy * S + k->rhi[i] + 1;
+        p->htab[2 * i] = dy * SP + k->rlo[i];
+        p->htab[2 * i + 1] = dy * SP + k->rhi[i] + 1;
         p->spans[i] = (int)((uint32_t)(k->rlo[i] & 0xffff) | ((uint32_t)k->rhi[i] << 16));
     }
-    // Shared memory: [keys | ordinal image] [A] [B] [histograms | medians + seed histograms] [spans]
-    const size_t area = (size_t)S * p->SH;
-    const size_t keyb = (size_t)elem_size(dtype);
+    p->sort = dtype == FIM_U8 ? kSortCount8 : (dtype == FIM_U16 ? kSortCount16 : kSortRadix);
+    // Shared memory. Tables and the omnigram live for the whole kernel; the work region holds
+    // the sort's buffers first and then the solve's (ordinal image, medians, seed histograms).
     size_t off = 0;
-    p->off_keys = (int)off;
-    off += align16(area * std::max<size_t>(keyb, 2));
-    p->off_a = (int)off;
-    off += align16((size_t)p->N * 2);
-    p->off_b = (int)off;
-    off += align16((size_t)p->N * 2);
-    p->off_h = (int)off;
-    const size_t hsort = (size_t)kSortBins * p->nwarps * 4;
-    const size_t hsolve = align16((size_t)T * T * 2) + (size_t)kSeedBins * p->nwarps * 4;
-    off += align16(std::max(hsort, hsolve));
-    p->off_spans = (int)off;
-    off += align16((size_t)p->nrows * 4);
+    auto take = [&](int* field, size_t bytes) {
+        *field = (int)off;
+        off += align16(bytes);
+    };
+    take(&p->off_vtab, (size_t)p->ncols * 8);
+    take(&p->off_htab, (size_t)p->nrows * 8);
+    take(&p->off_spans, (size_t)p->nrows * 4);
+    take(&p->off_frow, (size_t)p->SH * 4);
+    const size_t om_bytes = align16((size_t)p->N * 2);
+    const size_t ord_bytes = align16((size_t)SP * p->SH * 2);
+    const size_t med_bytes = align16((size_t)Tx * Ty * 2);
+    const size_t shist_bytes = (size_t)kSeedBins * p->nwarps * 4;
+    if (p->sort != kSortRadix) {
+        take(&p->off_om, om_bytes);
+        const size_t work = off;
+        const size_t bins = p->sort == kSortCount8 ? 256 * 4 : 32768 * 4;
+        p->off_bins = (int)work;
+        p->off_ord = (int)work;
+        p->off_med = (int)(work + ord_bytes);
+        p->off_shist = (int)(work + ord_bytes + med_bytes);
+        off = work + std::max(bins, ord_bytes + med_bytes + shist_bytes);
+        p->off_keys = p->off_a = p->off_b = p->off_hist = -1;
+    } else {
+        const size_t area = (size_t)S * p->SH;
+        take(&p->off_keys, std::max(area * 4, ord_bytes));
+        take(&p->off_a, om_bytes);
+        take(&p->off_b, om_bytes);
+        p->off_om = p->off_a;  // four passes end in B; the omnigram is then written into A
+        p->off_ord = p->off_keys;
+        const size_t hist = (size_t)p->nwarps * (kSortBins + 1) * 4;
+        p->off_hist = (int)off;
+        p->off_med = (int)off;
+        p->off_shist = (int)(off + med_bytes);
+        off += align16(std::max(hist, med_bytes + shist_bytes));
+        p->off_bins = -1;
+    }
     if (off > (size_t)1 << 30) return FIM_ERR_UNSUPPORTED;
-    p->smem_bytes = (int)off;
+    p->smem_bytes = (int)align16(off);
     return FIM_OK;
 }
 
+static bool parse_tile_env(TileShape* ts) {
+    const char* e = getenv("FIM_TILE");
+    if (!e || !*e) return false;
+    int a, b, c, d;
+    if (sscanf(e, "%d,%d,%d,%d", &a, &b, &c, &d) != 4) return false;
+    *ts = TileShape{a, b, c, d};
+    return true;
+}
+
 fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts) {
-    static const TileShape cands[] = {{64, 8, 4}, {32, 8, 4}};
-    for (const TileShape& c : cands) {
+    static const TileShape cands[] = {{64, 128, 8, 2}, {64, 64, 8, 2}, {32, 64, 8, 2}, {32, 32, 8, 2}};
+    TileShape forced;
+    if (parse_tile_env(&forced)) {  // explicit override (experiments, tuning)
+        Plan* p = new (std::nothrow) Plan;
+        if (!p) return FIM_ERR_OOM;
+        fim_status s = make_plan(k, dtype, 0, 1, 1, forced, p);
+        const int bytes = p->smem_bytes;
+        delete p;
+        if (s != FIM_OK) return s;
+        if (bytes > smem_limit) return FIM_ERR_UNSUPPORTED;
+        *ts = forced;
+        return FIM_OK;
+    }
+    // Taller tiles halve the seed and seed-row work per pixel but enlarge the footprint, which
+    // lengthens every refinement scan; they pay off once the kernel is large (measured on the
+    // 4096^2 photo-like workload: 64x128 is best from r = 48 on, 64x64 below).
+    const int extent = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1;
+    const int first = extent >= 81 ? 0 : 1;
+    for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
+        const TileShape& c = cands[i];
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
         fim_status s = make_plan(k, dtype, 0, 1, 1, c, p);
@@ -199,6 +261,26 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     return FIM_ERR_UNSUPPORTED;
 }
 
+}  // namespace fim
+
+namespace fim {
+namespace {
+std::mutex g_diag_mu;
+unsigned long long* g_phase_buf = nullptr;
+int g_phase_tiles = 0;
+}  // namespace
+
+void set_phase_clock_buffer(unsigned long long* buf, int tiles) {
+    std::lock_guard<std::mutex> g(g_diag_mu);
+    g_phase_buf = buf;
+    g_phase_tiles = buf ? tiles : 0;
+}
+
+void get_phase_clock_buffer(unsigned long long** buf, int* tiles) {
+    std::lock_guard<std::mutex> g(g_diag_mu);
+    *buf = g_phase_buf;
+    *tiles = g_phase_tiles;
+}
 }  // namespace fim
 
 using namespace fim;
@@ -247,6 +329,7 @@ fim_status filter_rank(const void* in, void* out, int w, int h, size_t pitch, in
         p->in = in;
         p->out = out;
         p->pitch = (long long)pitch;
+        get_phase_clock_buffer(&p->phase_clock, &p->phase_tiles);
         s = launch_tile_kernel(*p, stream);
     }
     delete p;
@@ -429,6 +512,28 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
 
 fim_status fim_sync_status(void* stream) { return read_and_clear_device_status((cudaStream_t)stream); }
 
+fim_status fim_plan_info(const fim_kernel* k, fim_dtype dtype, int w, int h, int* tile_w, int* tile_h,
+                         int* footprint, int* threads, int* smem_bytes) {
+    if (!k || w <= 0 || h <= 0 || (dtype != FIM_U8 && dtype != FIM_U16 && dtype != FIM_F32)) return FIM_ERR_INVALID_ARG;
+    const int limit = device_smem_limit();
+    if (limit <= 0) return FIM_ERR_CUDA;
+    TileShape ts;
+    fim_status s = choose_tile(k, dtype, limit, &ts);
+    if (s != FIM_OK) return s;
+    Plan* p = new (std::nothrow) Plan;
+    if (!p) return FIM_ERR_OOM;
+    s = make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, p);
+    if (s == FIM_OK) {
+        if (tile_w) *tile_w = p->Tx;
+        if (tile_h) *tile_h = p->Ty;
+        if (footprint) *footprint = p->N;
+        if (threads) *threads = p->threads;
+        if (smem_bytes) *smem_bytes = p->smem_bytes;
+    }
+    delete p;
+    return s;
+}
+
 const char* fim_status_string(fim_status s) {
     switch (s) {
         case FIM_OK: return "FIM_OK";
@@ -443,5 +548,11 @@ const char* fim_status_string(fim_status s) {
 }
 
 const char* fim_version(void) { return "0.1.0"; }
+
+fim_status fim_debug_phase_clocks(void* dev_buf, int tiles) {
+    if ((dev_buf == nullptr) != (tiles <= 0)) return FIM_ERR_INVALID_ARG;
+    set_phase_clock_buffer((unsigned long long*)dev_buf, tiles);
+    return FIM_OK;
+}
 
 }  // extern "C"

@@ -18,15 +18,22 @@ constexpr int kSeedBins = 256;    // coarse histogram bins of a seed solve
 
 enum Shape : int { kShapeDisk = 0, kShapeSpans = 1 };
 
-// Geometry of one tile configuration: output tile T x T, 2*T*RB threads.
-// RB bands of T/RB rows; each band's middle row is a seed row with G seeds.
+// Geometry of one tile configuration: output tile Tx x Ty, 2*Tx*RB threads.
+// RB bands of Ty/RB rows; each band's middle row is a seed row with G seeds.
 struct TileShape {
-    int T;
+    int Tx, Ty;
     int RB;
     int G;
 };
 
+enum SortKind : int {
+    kSortCount8 = 0,   // 256-bin counting sort (8-bit data)
+    kSortCount16 = 1,  // 65536-bin counting sort with packed 16-bit bins (16-bit data, Eq. 5)
+    kSortRadix = 2     // stable LSD radix sort, four 8-bit passes (32-bit float keys)
+};
+
 // Everything a tile kernel launch needs, passed by value as a __grid_constant__ parameter.
+// Scalars are read at static offsets; the tables are copied into shared memory once per CTA.
 struct Plan {
     // image
     const void* in;
@@ -35,8 +42,9 @@ struct Plan {
     int w, h;
     int dtype;
     // tiling
-    int T, RB, G, threads, nwarps;
+    int Tx, Ty, txshift, RB, G, threads, nwarps;
     int S, SH;              // footprint bounding box (columns, rows)
+    int SP;                 // row pitch (elements) of the ordinal image; SP/2 is odd
     int tiles_x, tiles_y;
     // kernel
     int shape;
@@ -47,13 +55,22 @@ struct Plan {
     // footprint
     int N;                  // pixels in the rounded-rectangle footprint
     int cx0, cy0;           // omnigram coordinates are stored as (u - cx0, v - cy0), int8 each
-    unsigned div_magic;     // ceil(2^32 / S): v = umulhi(pos, magic) for pos < 2^16
+    unsigned div_magic;     // ceil(2^32 / S): v = umulhi(pos, magic) for pos < 2^16 (radix path)
     int hist_shift;         // seed histogram: bin = rank >> hist_shift
+    int sort;               // SortKind
+    unsigned long long* phase_clock;  // optional: 8 clock64() stamps per tile (diagnostics)
+    int phase_tiles;                  // capacity of phase_clock in tiles
     // dynamic shared memory layout (byte offsets)
-    int off_keys, off_a, off_b, off_h, off_spans, smem_bytes;
-    int16_t fl[kMaxSide], fr[kMaxSide];   // footprint row v covers u in [fl[v], fr[v]]
-    int vA[kMaxExtent], vB[kMaxExtent];   // per column j: top*S + dx, (bot+1)*S + dx
-    int hL[kMaxExtent], hH[kMaxExtent];   // per row i: dy*S + lo, dy*S + hi + 1
+    int off_vtab, off_htab, off_spans, off_frow;  // tables (whole kernel)
+    int off_om;                                    // omnigram, N x u16 (from the sort on)
+    int off_bins;                                  // counting sorts: bins
+    int off_keys, off_a, off_b, off_hist;          // radix sort: keys, ping-pong lists, histograms
+    int off_ord, off_med, off_shist;               // solve: ordinal image, medians, seed histograms
+    int smem_bytes;
+    // tables (copied to shared memory at kernel start)
+    int frow[kMaxSide];                   // footprint row v covers u in [lo, hi]: lo | hi << 16
+    int vtab[2 * kMaxExtent];             // per column j: top*SP + dx, (bot+1)*SP + dx
+    int htab[2 * kMaxExtent];             // per row i: dy*SP + lo, dy*SP + hi + 1
     int spans[kMaxExtent];                // per row i: (lo & 0xffff) | (hi << 16)
 };
 
@@ -75,6 +92,10 @@ namespace fim {
 fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, Plan* p);
 fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts);
 int device_smem_limit();
+
+// Diagnostics: device buffer that receives per-phase clock64() stamps (may be null).
+void set_phase_clock_buffer(unsigned long long* buf, int tiles);
+void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 
 // Device launch (fim_tile.cu).
 fim_status launch_tile_kernel(const Plan& p, cudaStream_t stream);
