@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=1024, help="rows of the image in the CPU oracle sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batched comparison")
     ap.add_argument("--profile-case", default=None, metavar="SIDE:R",
                     help="only run two launches on a SIDE x SIDE crop of the image at radius R (for ncu)")
     return ap.parse_args()
@@ -195,6 +196,89 @@ def cpu_oracle_sample(img, rows: int):
     return {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
             "sample": f"rows {y0}..{y0 + rows - 1} x all 4096 columns of the same image at r=8,32,48 "
                       f"({px} output pixels, {dt:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------------------------
+# batched persistent launch vs sequential plain launches (64 mixed images)
+# ---------------------------------------------------------------------------------------------
+
+def batched_section(fim, torch, reps: int = 3):
+    """64 images (sides 512-4096, u8/u16/f32, disk r log-uniform in [2, 128]); tile shapes
+    autotuned per (dtype, radius) on a 512x512 crop; one CUDA-graph-captured persistent launch
+    against the same filters issued as one launch per image. Outputs are compared bytewise."""
+    import datagen
+    codes = {"u8": fim.FIM_U8, "u16": fim.FIM_U16, "f32": fim.FIM_F32}
+    esz = {"u8": 1, "u16": 2, "f32": 4}
+    jobs = datagen.config5_jobs()
+    t0 = time.perf_counter()
+    imgs = [datagen.torch_config5_image(j) for j in jobs]
+    outs_b = [torch.empty_like(x) for x in imgs]
+    outs_s = [torch.empty_like(x) for x in imgs]
+    kern = {}
+    for j in jobs:
+        kern.setdefault(j["r"], fim.fim_create_kernel_circle(j["r"]))
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    # autotune every (dtype, radius) pair on a 512x512 crop of its first image
+    t0 = time.perf_counter()
+    tuned = {}
+    for j, x in zip(jobs, imgs):
+        key = (j["dtype"], j["r"])
+        if key in tuned:
+            continue
+        crop = x[:512, :512].contiguous()
+        tmp = torch.empty_like(crop)
+        args = (crop.data_ptr(), tmp.data_ptr(), crop.shape[1], crop.shape[0], crop.stride(0) * esz[j["dtype"]],
+                codes[j["dtype"]], kern[j["r"]], sh)
+        tuned[key] = fim.fim_autotune(*args)                    # for single-image launches
+        try:
+            fim.fim_autotune(*args, cta_threads=1024)           # for the batch's common CTA size
+        except fim.FimError:
+            pass
+    tune_s = time.perf_counter() - t0
+    cjobs = [fim.make_job(x.data_ptr(), o.data_ptr(), j["w"], j["h"], x.stride(0) * esz[j["dtype"]],
+                          codes[j["dtype"]], kern[j["r"]]) for j, x, o in zip(jobs, imgs, outs_b)]
+    batch = fim.fim_batch_create(cjobs, list(kern.values()))
+
+    def sequential():
+        for j, x, o in zip(jobs, imgs, outs_s):
+            fim.fim_median(x.data_ptr(), o.data_ptr(), j["w"], j["h"], x.stride(0) * esz[j["dtype"]],
+                           codes[j["dtype"]], kern[j["r"]], sh)
+
+    sequential()
+    batch.run(sh)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(stream)
+    with torch.cuda.graph(g, stream=cap):
+        batch.run(int(cap.cuda_stream))
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        best = []
+        for _ in range(reps):
+            s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_ev.record(stream)
+            fn()
+            e_ev.record(stream)
+            torch.cuda.synchronize()
+            best.append(s_ev.elapsed_time(e_ev))
+        return sum(best) / len(best)
+
+    ms_seq = timed(sequential)
+    ms_bat = timed(g.replay)
+    status = fim.fim_sync_status(sh)
+    same = all(torch.equal(a.view(torch.uint8), b.view(torch.uint8)) for a, b in zip(outs_b, outs_s))
+    mpix = sum(j["w"] * j["h"] for j in jobs) / 1e6
+    return {"workload": "64 images, sides U{512..4096}, dtypes u8/u16/f32, disk r log-uniform [2,128]",
+            "mpix": round(mpix, 2), "value": mpix / (ms_bat * 1e-3), "unit": "Mpix/s",
+            "sequential_Mpix_s": mpix / (ms_seq * 1e-3), "speedup": ms_seq / ms_bat,
+            "ms_batched_graph": ms_bat, "ms_sequential": ms_seq, "launches_batched": 1,
+            "launches_sequential": len(jobs), "bit_exact_vs_sequential": bool(same), "status": status,
+            "tiles": batch.info["total_tiles"], "autotune_s": round(tune_s, 2), "generate_s": round(gen_s, 2)}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -377,6 +461,8 @@ def run_native(args):
         "roofline": roofline,
         "clocks": clk,
     }
+    if world == 1 and not args.no_batched:
+        line["batched"] = batched_section(fim, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(img, args.cpu_rows)
     if rank == 0:

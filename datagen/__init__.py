@@ -203,3 +203,78 @@ def adversarial_tile(h: int, w: int, dtype: str = "u16", border: int = 24) -> np
     frame = (xx < border) | (yy < border) | (xx >= w - border) | (yy >= h - border)
     img[frame] = mid
     return img
+
+
+# --------------------------------------------------------------------------------------
+# The same recipes drawn on a CUDA device with torch (fast inputs for large benchmarks).
+# Same structure and parameters; the random streams differ from the numpy versions.
+# --------------------------------------------------------------------------------------
+
+def _torch_field(gen, h, w, sigma, device):
+    import torch
+    noise = torch.randn((h, w), generator=gen, device=device, dtype=torch.float32)
+    fy = torch.fft.fftfreq(h, device=device)[:, None]
+    fx = torch.fft.rfftfreq(w, device=device)[None, :]
+    g = torch.exp(-2.0 * math.pi ** 2 * sigma ** 2 * (fy * fy + fx * fx))
+    out = torch.fft.irfft2(torch.fft.rfft2(noise) * g, s=(h, w))
+    fxf = torch.fft.fftfreq(w, device=device, dtype=torch.float64)[None, :]
+    gfull = torch.exp(-2.0 * math.pi ** 2 * sigma ** 2 * (fy.double() ** 2 + fxf * fxf))
+    return out / math.sqrt(float((gfull * gfull).mean()))
+
+
+def torch_photo_u16(seed: int, h: int, w: int, device="cuda", n_polygons: int = 32, impulse_frac: float = 0.05):
+    """photo_u16's recipe on the GPU (int16 storage view of uint16 data is returned as torch.uint16)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    f = sum(_torch_field(gen, h, w, s, device) for s in (2.0, 16.0, 64.0))
+    img = 32768.0 + (8192.0 / math.sqrt(3.0)) * f
+    rng = _rng(seed)
+    rscale = math.sqrt(h * w) / 4096.0
+    yy = torch.arange(h, device=device, dtype=torch.float32)[:, None]
+    xx = torch.arange(w, device=device, dtype=torch.float32)[None, :]
+    for _ in range(n_polygons):
+        nv = int(rng.integers(3, 9))
+        rad = float(rng.uniform(64, 1024)) * rscale
+        cx, cy = float(rng.uniform(0, w)), float(rng.uniform(0, h))
+        ang = np.sort(rng.uniform(0, 2 * math.pi, nv))
+        vx, vy = cx + rad * np.cos(ang), cy + rad * np.sin(ang)
+        inside = torch.ones((h, w), dtype=torch.bool, device=device)
+        for i in range(nv):
+            ax, ay, bx, by = vx[i], vy[i], vx[(i + 1) % nv], vy[(i + 1) % nv]
+            inside &= (bx - ax) * (yy - ay) - (by - ay) * (xx - ax) >= 0
+        img += inside.float() * float(rng.uniform(-12000, 12000))
+    out = torch.clamp(torch.round(img), 0, 65535).to(torch.int32)
+    imp = torch.rand((h, w), generator=gen, device=device) < impulse_frac
+    hi = torch.rand((h, w), generator=gen, device=device) < 0.5
+    out = torch.where(imp, torch.where(hi, 65535, 0), out)
+    return out.to(torch.int32).to(torch.uint16) if hasattr(torch, "uint16") else out
+
+
+def torch_field_f32(seed: int, h: int, w: int, device="cuda", outlier_frac: float = 0.01, cauchy_scale: float = 10.0):
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    f = sum(_torch_field(gen, h, w, s, device) for s in (2.0, 16.0, 64.0))
+    f = f / max(float(f.std()), 1e-30)
+    mask = torch.rand((h, w), generator=gen, device=device) < outlier_frac
+    u = torch.rand((h, w), generator=gen, device=device, dtype=torch.float64)
+    c = torch.clamp(cauchy_scale * torch.tan(math.pi * (u - 0.5)), -1e30, 1e30).float()
+    f = torch.where(mask, f + c, f)
+    f = torch.nan_to_num(f, nan=0.0, posinf=0.0, neginf=0.0)
+    return f + 0.0
+
+
+def torch_uniform_u8(seed: int, h: int, w: int, device="cuda"):
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    return torch.randint(0, 256, (h, w), generator=gen, device=device, dtype=torch.uint8)
+
+
+def torch_config5_image(job: dict, device="cuda"):
+    if job["dtype"] == "u8":
+        return torch_uniform_u8(job["seed"], job["h"], job["w"], device)
+    if job["dtype"] == "u16":
+        return torch_photo_u16(job["seed"], job["h"], job["w"], device)
+    return torch_field_f32(job["seed"], job["h"], job["w"], device)

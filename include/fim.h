@@ -118,6 +118,61 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
                            fim_dtype dtype, const fim_kernel* k, fim_border border, void* stream);
 
 /*
+ * Tunes the tile configuration for (current device, dtype, kernel geometry): every valid
+ * configuration is run on this image (in -> out, which ends up holding the filtered image) and
+ * timed with CUDA events; the fastest is kept in a process-wide cache that later fim_median,
+ * fim_percentile and batch calls with the same dtype and kernel geometry use. cta_threads = 0
+ * tunes over all CTA sizes; 256, 512 or 1024 restricts the search to that CTA size and stores
+ * the result separately (batches look up 1024 first: all jobs of a batch share one CTA size).
+ * If the environment variable FIM_TUNE_CACHE names a file, the cache is loaded from it on first
+ * use and rewritten after each tuning. tile_w / tile_h (may be NULL) receive the chosen tile.
+ * Synchronous. Not part of the paper: its GPU tiling is fixed by radius (Sec. 4.2).
+ */
+fim_status fim_autotune(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                        const fim_kernel* k, int cta_threads, void* stream, int* tile_w, int* tile_h);
+
+/* Forgets every tuned configuration of this process (the cache file is left alone). */
+fim_status fim_autotune_clear(void);
+
+/*
+ * Batched persistent launch. One job is one 2-D image filtered with its own kernel, dtype, size
+ * and pitch; percentile < 0 selects the median, otherwise the percentile filter of fim_percentile.
+ * All tiles of all jobs form one device-side queue worked off by one persistent launch
+ * (expensive tiles first). Not part of the paper.
+ */
+typedef struct {
+    const void* in;      /* device pointer */
+    void* out;           /* device pointer, must not overlap any input */
+    int w, h;
+    size_t pitch_bytes;  /* input and output */
+    fim_dtype dtype;
+    const fim_kernel* kernel;
+    double percentile;   /* < 0: median */
+} fim_job;
+
+typedef struct fim_batch fim_batch;
+
+/*
+ * Plans a batch: validates every job, picks tile configurations (tuned ones when available),
+ * uploads the per-job plans and allocates the batch's workspace. Synchronous. The images are
+ * only referenced: they must stay valid while the batch runs.
+ */
+fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out);
+
+/* Runs a batch on `stream`: one memset of the queue counter and one kernel launch, both stream
+ * operations (graph-capturable). Runs of one batch must not overlap in time. */
+fim_status fim_batch_run(fim_batch* b, void* stream);
+
+/* Size of a batch launch: total queued tiles, CTAs, threads per CTA, shared memory per CTA. */
+fim_status fim_batch_info(const fim_batch* b, int* total_tiles, int* grid, int* threads, int* smem_bytes);
+
+/* Waits for the device, then frees the batch (NULL is ignored). */
+void fim_batch_destroy(fim_batch* b);
+
+/* One-shot: fim_batch_create + fim_batch_run + wait for `stream` + fim_batch_destroy. */
+fim_status fim_median_batch(const fim_job* jobs, int count, void* stream);
+
+/*
  * Waits for `stream`, then returns and clears the device status word: FIM_OK, or the
  * first device-side error recorded since the last call (FIM_ERR_TIMEOUT, FIM_ERR_INTERNAL).
  */
@@ -132,6 +187,13 @@ fim_status fim_sync_status(void* stream);
  */
 fim_status fim_plan_info(const fim_kernel* k, fim_dtype dtype, int w, int h, int* tile_w, int* tile_h,
                          int* footprint, int* threads, int* smem_bytes);
+
+/*
+ * The filter keeps one device workspace per (device, stream) it has run on: the tile queue
+ * counter and, for kernels whose footprint does not fit in shared memory, per-CTA buffers.
+ * It grows on demand and lives until this call, which waits for the device and frees it.
+ */
+fim_status fim_release_workspace(void);
 
 /* Static, human-readable name of a status code. */
 const char* fim_status_string(fim_status s);

@@ -45,7 +45,22 @@ SIGNATURES = {
     "fim_version": (_c.c_char_p, []),
     "fim_debug_phase_clocks": (_c.c_int, [_P, _c.c_int]),
     "fim_plan_info": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P, _P, _P]),
+    "fim_release_workspace": (_c.c_int, []),
+    "fim_autotune": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P, _P, _P]),
+    "fim_autotune_clear": (_c.c_int, []),
+    "fim_batch_create": (_c.c_int, [_P, _c.c_int, _PP]),
+    "fim_batch_run": (_c.c_int, [_P, _P]),
+    "fim_batch_info": (_c.c_int, [_P, _P, _P, _P, _P]),
+    "fim_batch_destroy": (None, [_P]),
+    "fim_median_batch": (_c.c_int, [_P, _c.c_int, _P]),
 }
+
+
+class fim_job(ctypes.Structure):
+    """Mirror of the C struct fim_job."""
+    _fields_ = [("in_ptr", ctypes.c_void_p), ("out_ptr", ctypes.c_void_p), ("w", ctypes.c_int),
+                ("h", ctypes.c_int), ("pitch_bytes", ctypes.c_size_t), ("dtype", ctypes.c_int),
+                ("kernel", ctypes.c_void_p), ("percentile", ctypes.c_double)]
 
 _lock = threading.Lock()
 _lib = None
@@ -167,6 +182,69 @@ def fim_sync_status(stream: int = 0) -> int:
 
 def fim_status_string(code: int) -> str:
     return lib().fim_status_string(int(code)).decode()
+
+
+def fim_autotune(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+                 stream: int = 0, cta_threads: int = 0) -> tuple:
+    tw, th = ctypes.c_int(), ctypes.c_int()
+    _check(lib().fim_autotune(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, int(cta_threads),
+                              stream or None, ctypes.byref(tw), ctypes.byref(th)), "fim_autotune")
+    return tw.value, th.value
+
+
+def fim_autotune_clear() -> None:
+    _check(lib().fim_autotune_clear(), "fim_autotune_clear")
+
+
+class Batch:
+    """Owns a fim_batch handle (and keeps its kernels alive)."""
+
+    def __init__(self, jobs: list, kernels: list):
+        arr = (fim_job * len(jobs))(*jobs)
+        h = ctypes.c_void_p()
+        _check(lib().fim_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(jobs), ctypes.byref(h)),
+               "fim_batch_create")
+        self.handle = h
+        self._kernels = kernels
+
+    def run(self, stream: int = 0) -> None:
+        _check(lib().fim_batch_run(self.handle, stream or None), "fim_batch_run")
+
+    @property
+    def info(self) -> dict:
+        vals = [ctypes.c_int() for _ in range(4)]
+        _check(lib().fim_batch_info(self.handle, *[ctypes.byref(v) for v in vals]), "fim_batch_info")
+        return dict(zip(("total_tiles", "grid", "threads", "smem_bytes"), (v.value for v in vals)))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().fim_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_job(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+             percentile: float = -1.0) -> fim_job:
+    return fim_job(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, float(percentile))
+
+
+def fim_batch_create(jobs: list, kernels: list) -> Batch:
+    return Batch(jobs, kernels)
+
+
+def fim_median_batch(jobs: list, stream: int = 0) -> None:
+    arr = (fim_job * len(jobs))(*jobs)
+    _check(lib().fim_median_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs), stream or None),
+           "fim_median_batch")
+
+
+def fim_release_workspace() -> None:
+    _check(lib().fim_release_workspace(), "fim_release_workspace")
 
 
 def fim_version() -> str:

@@ -1,0 +1,161 @@
+// Batched persistent launch (host side): many images of any size, dtype and kernel share one
+// queue of tiles and one kernel launch. The batch object owns its device-side plans, the tile
+// prefix table and its workspace, so fim_batch_run() only zeroes the queue counter and launches:
+// both are stream operations and can be captured in a CUDA graph.
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "fim_internal.h"
+
+using namespace fim;
+
+struct fim_batch {
+    int njobs = 0;
+    int total_tiles = 0;
+    int grid = 0, threads = 0, smem = 0;
+    long long scratch_per_cta = 0;
+    Plan* d_plans = nullptr;
+    int* d_prefix = nullptr;
+    unsigned char* scratch = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+int esize(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); }
+
+// Relative cost of one tile, used only to start the expensive tiles first.
+double tile_cost(const Plan& p) {
+    const double px = (double)p.Tx * p.Ty;
+    const double sort = p.sort == kSortRadix ? 12.0 : 3.0;
+    return p.N * sort + px * (2.0 * p.ncols + 80.0) + (double)p.RB * p.G * p.n * 2.0;
+}
+
+void free_batch(fim_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->d_plans) cudaFree(b->d_plans);
+    if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->scratch) cudaFree(b->scratch);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
+    if (!out || !jobs || count <= 0) return FIM_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int limit = device_smem_limit();
+    if (limit <= 0) return FIM_ERR_CUDA;
+    std::vector<TileShape> shapes((size_t)count);
+    int cta = 32;
+    for (int i = 0; i < count; ++i) {
+        const fim_job& j = jobs[i];
+        if (!j.in || !j.out || !j.kernel || j.w <= 0 || j.h <= 0) return FIM_ERR_INVALID_ARG;
+        if (j.dtype != FIM_U8 && j.dtype != FIM_U16 && j.dtype != FIM_F32) return FIM_ERR_INVALID_ARG;
+        const size_t es = (size_t)esize(j.dtype);
+        if (j.pitch_bytes < (size_t)j.w * es || j.pitch_bytes % es != 0) return FIM_ERR_INVALID_ARG;
+        if (!(j.percentile < 0.0 || j.percentile <= 100.0)) return FIM_ERR_INVALID_ARG;
+        fim_status s = choose_tile(j.kernel, j.dtype, limit, &shapes[i], 1024);
+        if (s != FIM_OK) return s;
+        cta = std::max(cta, 2 * shapes[i].Tx * shapes[i].RB);
+    }
+    std::vector<Plan> plans((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const fim_job& j = jobs[i];
+        const int n = j.kernel->n;
+        int rank = (n - 1) / 2;
+        if (j.percentile >= 0.0) rank = std::min(std::max((int)(j.percentile / 100.0 * (n - 1) + 0.5), 0), n - 1);
+        fim_status s = make_plan(j.kernel, j.dtype, rank, j.w, j.h, shapes[i], limit, &plans[i], cta);
+        if (s != FIM_OK) return s;
+        plans[i].in = j.in;
+        plans[i].out = j.out;
+        plans[i].pitch = (long long)j.pitch_bytes;
+        plans[i].ntiles = plans[i].tiles_x * plans[i].tiles_y;
+    }
+    std::vector<int> order((size_t)count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return tile_cost(plans[a]) > tile_cost(plans[b]); });
+    std::vector<Plan> sorted((size_t)count);
+    std::vector<int> prefix((size_t)count + 1, 0);
+    long long total = 0;
+    long long spc = 0;
+    for (int i = 0; i < count; ++i) {
+        sorted[i] = plans[order[i]];
+        prefix[i] = (int)total;
+        total += sorted[i].ntiles;
+        spc = std::max(spc, sorted[i].scratch_per_cta);
+    }
+    if (total > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
+    prefix[count] = (int)total;
+    fim_batch* b = new (std::nothrow) fim_batch();
+    if (!b) return FIM_ERR_OOM;
+    cudaGetDevice(&b->device);
+    b->njobs = count;
+    b->total_tiles = (int)total;
+    b->scratch_per_cta = spc;
+    fim_status s = batch_prepare(sorted.data(), count, &b->smem, &b->threads);
+    if (s == FIM_OK) s = batch_grid(b->threads, b->smem, total, &b->grid);
+    if (s != FIM_OK) {
+        free_batch(b);
+        return s;
+    }
+    const size_t scratch_bytes = 256 + (size_t)b->grid * (size_t)spc;
+    if (cudaMalloc(&b->d_plans, sizeof(Plan) * (size_t)count) != cudaSuccess ||
+        cudaMalloc(&b->d_prefix, sizeof(int) * ((size_t)count + 1)) != cudaSuccess ||
+        cudaMalloc(&b->scratch, scratch_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return FIM_ERR_OOM;
+    }
+    if (cudaMemcpy(b->d_plans, sorted.data(), sizeof(Plan) * (size_t)count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * ((size_t)count + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        free_batch(b);
+        return FIM_ERR_CUDA;
+    }
+    *out = b;
+    return FIM_OK;
+}
+
+fim_status fim_batch_run(fim_batch* b, void* stream) {
+    if (!b) return FIM_ERR_INVALID_ARG;
+    BatchArgs a;
+    a.plans = b->d_plans;
+    a.prefix = b->d_prefix;
+    a.njobs = b->njobs;
+    a.total_tiles = b->total_tiles;
+    a.scratch = b->scratch;
+    a.scratch_per_cta = b->scratch_per_cta;
+    return batch_launch(a, b->grid, b->threads, b->smem, (cudaStream_t)stream);
+}
+
+fim_status fim_batch_info(const fim_batch* b, int* total_tiles, int* grid, int* threads, int* smem_bytes) {
+    if (!b) return FIM_ERR_INVALID_ARG;
+    if (total_tiles) *total_tiles = b->total_tiles;
+    if (grid) *grid = b->grid;
+    if (threads) *threads = b->threads;
+    if (smem_bytes) *smem_bytes = b->smem;
+    return FIM_OK;
+}
+
+void fim_batch_destroy(fim_batch* b) { free_batch(b); }
+
+fim_status fim_median_batch(const fim_job* jobs, int count, void* stream) {
+    fim_batch* b = nullptr;
+    fim_status s = fim_batch_create(jobs, count, &b);
+    if (s != FIM_OK) return s;
+    s = fim_batch_run(b, stream);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess && s == FIM_OK) s = FIM_ERR_CUDA;
+    fim_batch_destroy(b);
+    return s;
+}
+
+}  // extern "C"

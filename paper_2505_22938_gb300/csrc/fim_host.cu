@@ -95,6 +95,70 @@ fim_status disk_kernel(int64_t limit, fim_kernel** out) {
 
 }  // namespace
 
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+    if (dev < 64) cached[dev] = v;
+    return v;
+}
+
+namespace {
+// Global scratch of the tile kernels, cached per (device, stream). Launches on one stream run
+// in order, so they can share one buffer; a buffer is only replaced after its stream drained.
+struct ScratchBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_scratch_mu;
+std::map<std::pair<int, uintptr_t>, ScratchBuf>& scratch_map() {
+    static std::map<std::pair<int, uintptr_t>, ScratchBuf> m;
+    return m;
+}
+}  // namespace
+
+fim_status get_scratch(cudaStream_t stream, size_t bytes, unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FIM_ERR_CUDA;
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    ScratchBuf& b = scratch_map()[{dev, (uintptr_t)stream}];
+    if (b.bytes < bytes) {
+        if (b.ptr) {
+            if (cudaStreamSynchronize(stream) != cudaSuccess) return FIM_ERR_CUDA;
+            cudaFree(b.ptr);
+            b.ptr = nullptr;
+            b.bytes = 0;
+        }
+        const size_t want = std::max(bytes, (size_t)1 << 20);
+        if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+            cudaGetLastError();
+            b.ptr = nullptr;
+            return FIM_ERR_OOM;
+        }
+        b.bytes = want;
+    }
+    *out = static_cast<unsigned char*>(b.ptr);
+    return FIM_OK;
+}
+
+fim_status release_scratch() {
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return FIM_ERR_CUDA;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& kv : scratch_map()) {
+        if (kv.second.ptr) {
+            cudaSetDevice(kv.first.first);
+            cudaFree(kv.second.ptr);
+        }
+    }
+    scratch_map().clear();
+    cudaSetDevice(cur);
+    return FIM_OK;
+}
+
 int device_smem_limit() {
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -103,10 +167,12 @@ int device_smem_limit() {
 }
 
 static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+fim_status layout_plan(Plan* p, int smem_limit);
 
 static int elem_size(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); }
 
-fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, Plan* p) {
+fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, int smem_limit,
+                     Plan* p, int cta_threads) {
     memset(p, 0, sizeof(*p));
     p->dtype = dtype;
     p->w = w;
@@ -116,13 +182,14 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->txshift = 0;
     while ((1 << p->txshift) < ts.Tx) ++p->txshift;
     if ((1 << p->txshift) != ts.Tx || ts.Tx % 32 != 0 || ts.Ty % ts.RB != 0 || ts.Tx % ts.G != 0 ||
-        ts.Ty / ts.RB < 2 || ts.Tx / ts.G < 2)
+        ts.Ty / ts.RB < 1 || ts.Tx / ts.G < 2)
         return FIM_ERR_INTERNAL;
     p->RB = ts.RB;
     p->G = ts.G;
-    p->threads = 2 * ts.Tx * ts.RB;
+    p->vthreads = 2 * ts.Tx * ts.RB;
+    p->threads = std::max(p->vthreads, cta_threads);
     p->nwarps = p->threads / 32;
-    if (p->threads > 1024 || p->nwarps > 32) return FIM_ERR_INTERNAL;
+    if (p->threads > 1024 || p->threads % 32 != 0) return FIM_ERR_INTERNAL;
     p->shape = k->shape;
     p->r2 = (int)k->r2;
     p->xmin = k->xmin;
@@ -135,7 +202,8 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->rank = rank;
     p->S = ts.Tx + (k->xmax - k->xmin);
     p->SH = ts.Ty + (k->ymax - k->ymin);
-    if (p->S > 256 || p->SH > 256 || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
+    if (p->S > kMaxSide || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
+    p->wide = (p->S > 256 || p->SH > 256) ? 1 : 0;
     p->SP = (p->S + 1) & ~1;
     if ((p->SP / 2) % 2 == 0) p->SP += 2;  // odd number of 32-bit words per row: no bank aliasing
     p->tiles_x = (w + ts.Tx - 1) / ts.Tx;
@@ -174,47 +242,99 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
         p->spans[i] = (int)((uint32_t)(k->rlo[i] & 0xffff) | ((uint32_t)k->rhi[i] << 16));
     }
     p->sort = dtype == FIM_U8 ? kSortCount8 : (dtype == FIM_U16 ? kSortCount16 : kSortRadix);
-    // Shared memory. Tables and the omnigram live for the whole kernel; the work region holds
-    // the sort's buffers first and then the solve's (ordinal image, medians, seed histograms).
-    size_t off = 0;
-    auto take = [&](int* field, size_t bytes) {
-        *field = (int)off;
-        off += align16(bytes);
-    };
-    take(&p->off_vtab, (size_t)p->ncols * 8);
-    take(&p->off_htab, (size_t)p->nrows * 8);
-    take(&p->off_spans, (size_t)p->nrows * 4);
-    take(&p->off_frow, (size_t)p->SH * 4);
-    const size_t om_bytes = align16((size_t)p->N * 2);
+    // Placement. Tables, the ordinal image, medians and histograms always live in shared memory;
+    // the omnigram, the radix keys and the radix position lists go to the CTA's global scratch
+    // slice when shared memory cannot hold them (large kernels).
+    return layout_plan(p, smem_limit);
+}
+
+fim_status layout_plan(Plan* p, int smem_limit) {
+    const int Tx = p->Tx, Ty = p->Ty, SP = p->SP;
+    const size_t omb = p->wide ? 4 : 2;      // omnigram entry / position bytes
+    const size_t om_bytes = align16((size_t)p->N * omb);
     const size_t ord_bytes = align16((size_t)SP * p->SH * 2);
     const size_t med_bytes = align16((size_t)Tx * Ty * 2);
-    const size_t shist_bytes = (size_t)kSeedBins * p->nwarps * 4;
+    const size_t shist_bytes = (size_t)kSeedBins * std::min(p->nwarps, p->RB * p->G) * 4;
+    const size_t solve_bytes = ord_bytes + med_bytes + shist_bytes;
+    size_t tab = 0;
+    auto take_tab = [&](int* field, size_t bytes) {
+        *field = (int)tab;
+        tab += align16(bytes);
+    };
+    take_tab(&p->off_vtab, (size_t)p->ncols * 8);
+    take_tab(&p->off_htab, (size_t)p->nrows * 8);
+    take_tab(&p->off_spans, (size_t)p->nrows * 4);
+    take_tab(&p->off_frow, (size_t)p->SH * 4);
+    auto gloc = [](size_t off) { return -(int)off - 1; };
+    p->loc_bins = p->loc_keys = p->loc_a = p->loc_b = p->loc_hist = 0;
+    size_t glob = 0;
+    auto take_glob = [&](size_t bytes) {
+        const size_t o = glob;
+        glob += (bytes + 255) & ~(size_t)255;
+        return gloc(o);
+    };
+    size_t smem = 0;
     if (p->sort != kSortRadix) {
-        take(&p->off_om, om_bytes);
-        const size_t work = off;
         const size_t bins = p->sort == kSortCount8 ? 256 * 4 : 32768 * 4;
-        p->off_bins = (int)work;
-        p->off_ord = (int)work;
-        p->off_med = (int)(work + ord_bytes);
-        p->off_shist = (int)(work + ord_bytes + med_bytes);
-        off = work + std::max(bins, ord_bytes + med_bytes + shist_bytes);
-        p->off_keys = p->off_a = p->off_b = p->off_hist = -1;
+        const size_t uni = std::max(bins, solve_bytes);
+        const bool om_smem = !p->wide && tab + om_bytes + uni <= (size_t)smem_limit;
+        size_t off = tab;
+        if (om_smem) {
+            p->loc_om = (int)off;
+            off += om_bytes;
+        } else {
+            p->loc_om = take_glob(om_bytes);
+        }
+        p->loc_bins = (int)off;
+        p->loc_ord = (int)off;
+        p->loc_med = (int)(off + ord_bytes);
+        p->loc_shist = (int)(off + ord_bytes + med_bytes);
+        smem = off + uni;
     } else {
-        const size_t area = (size_t)S * p->SH;
-        take(&p->off_keys, std::max(area * 4, ord_bytes));
-        take(&p->off_a, om_bytes);
-        take(&p->off_b, om_bytes);
-        p->off_om = p->off_a;  // four passes end in B; the omnigram is then written into A
-        p->off_ord = p->off_keys;
-        const size_t hist = (size_t)p->nwarps * (kSortBins + 1) * 4;
-        p->off_hist = (int)off;
-        p->off_med = (int)off;
-        p->off_shist = (int)(off + med_bytes);
-        off += align16(std::max(hist, med_bytes + shist_bytes));
-        p->off_bins = -1;
+        const size_t keys_bytes = align16((size_t)p->S * p->SH * 4);
+        const size_t hist_bytes = align16((size_t)p->nwarps * (kSortBins + 1) * 4);
+        // try: everything in shared memory; keys in global; keys and lists in global
+        int mode = 0;
+        for (mode = 0; mode < 3; ++mode) {
+            if (mode < 2 && p->wide) continue;  // 32-bit lists of a wide box never fit
+            size_t need = tab;
+            if (mode < 2) need += om_bytes;       // B / omnigram
+            const size_t sort_part = (mode == 0 ? keys_bytes : 0) + (mode < 2 ? om_bytes : 0) + hist_bytes;
+            need += std::max(sort_part, solve_bytes);
+            if (need <= (size_t)smem_limit) break;
+        }
+        if (mode == 3) return FIM_ERR_UNSUPPORTED;
+        size_t off = tab;
+        if (mode < 2) {
+            p->loc_b = (int)off;
+            off += om_bytes;
+        } else {
+            p->loc_b = take_glob(om_bytes);
+        }
+        p->loc_om = p->loc_b;  // the sorted positions are turned into the omnigram in place
+        const size_t uni = off;
+        if (mode == 0) {
+            p->loc_keys = (int)off;
+            off += keys_bytes;
+        } else {
+            p->loc_keys = take_glob(keys_bytes);
+        }
+        if (mode < 2) {
+            p->loc_a = (int)off;
+            off += om_bytes;
+        } else {
+            p->loc_a = take_glob(om_bytes);
+        }
+        p->loc_hist = (int)off;
+        off += hist_bytes;
+        p->loc_ord = (int)uni;
+        p->loc_med = (int)(uni + ord_bytes);
+        p->loc_shist = (int)(uni + ord_bytes + med_bytes);
+        smem = std::max(off, uni + solve_bytes);
     }
-    if (off > (size_t)1 << 30) return FIM_ERR_UNSUPPORTED;
-    p->smem_bytes = (int)align16(off);
+    if (smem > (size_t)smem_limit) return FIM_ERR_UNSUPPORTED;
+    p->smem_bytes = (int)align16(smem);
+    p->scratch_per_cta = (long long)glob;
     return FIM_OK;
 }
 
@@ -227,19 +347,32 @@ static bool parse_tile_env(TileShape* ts) {
     return true;
 }
 
-fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts) {
-    static const TileShape cands[] = {{64, 128, 8, 2}, {64, 64, 8, 2}, {32, 64, 8, 2}, {32, 32, 8, 2}};
+fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int cta_threads) {
+    static const TileShape cands[] = {{64, 128, 8, 2}, {64, 64, 8, 2}, {32, 64, 8, 2}, {32, 32, 8, 2},
+                                      {32, 16, 8, 2}};
     TileShape forced;
     if (parse_tile_env(&forced)) {  // explicit override (experiments, tuning)
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
-        fim_status s = make_plan(k, dtype, 0, 1, 1, forced, p);
+        fim_status s = make_plan(k, dtype, 0, 1, 1, forced, smem_limit, p);
         const int bytes = p->smem_bytes;
         delete p;
         if (s != FIM_OK) return s;
         if (bytes > smem_limit) return FIM_ERR_UNSUPPORTED;
         *ts = forced;
         return FIM_OK;
+    }
+    TileShape tuned;
+    // configuration chosen by fim_autotune: for this CTA size first, then for any size
+    if ((cta_threads > 0 && tuned_lookup(k, dtype, &tuned, cta_threads)) || tuned_lookup(k, dtype, &tuned, 0)) {
+        Plan* p = new (std::nothrow) Plan;
+        if (!p) return FIM_ERR_OOM;
+        fim_status s = make_plan(k, dtype, 0, 1, 1, tuned, smem_limit, p);
+        delete p;
+        if (s == FIM_OK) {
+            *ts = tuned;
+            return FIM_OK;
+        }
     }
     // Taller tiles halve the seed and seed-row work per pixel but enlarge the footprint, which
     // lengthens every refinement scan; they pay off once the kernel is large (measured on the
@@ -250,7 +383,7 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
         const TileShape& c = cands[i];
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
-        fim_status s = make_plan(k, dtype, 0, 1, 1, c, p);
+        fim_status s = make_plan(k, dtype, 0, 1, 1, c, smem_limit, p);
         const int bytes = p->smem_bytes;
         delete p;
         if (s == FIM_OK && bytes <= smem_limit) {
@@ -324,7 +457,7 @@ fim_status filter_rank(const void* in, void* out, int w, int h, size_t pitch, in
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
-    s = make_plan(k, dtype, rank, w, h, ts, p);
+    s = make_plan(k, dtype, rank, w, h, ts, smem_limit, p);
     if (s == FIM_OK) {
         p->in = in;
         p->out = out;
@@ -522,7 +655,7 @@ fim_status fim_plan_info(const fim_kernel* k, fim_dtype dtype, int w, int h, int
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
-    s = make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, p);
+    s = make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, limit, p);
     if (s == FIM_OK) {
         if (tile_w) *tile_w = p->Tx;
         if (tile_h) *tile_h = p->Ty;
@@ -548,6 +681,8 @@ const char* fim_status_string(fim_status s) {
 }
 
 const char* fim_version(void) { return "0.1.0"; }
+
+fim_status fim_release_workspace(void) { return release_scratch(); }
 
 fim_status fim_debug_phase_clocks(void* dev_buf, int tiles) {
     if ((dev_buf == nullptr) != (tiles <= 0)) return FIM_ERR_INVALID_ARG;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -42,7 +43,9 @@ struct Plan {
     int w, h;
     int dtype;
     // tiling
-    int Tx, Ty, txshift, RB, G, threads, nwarps;
+    int Tx, Ty, txshift, RB, G;
+    int threads, nwarps;    // CTA size (all cooperative loops and per-warp buffers)
+    int vthreads;           // 2*Tx*RB: threads of the vertical sweep (the first ones of the CTA)
     int S, SH;              // footprint bounding box (columns, rows)
     int SP;                 // row pitch (elements) of the ordinal image; SP/2 is odd
     int tiles_x, tiles_y;
@@ -58,20 +61,36 @@ struct Plan {
     unsigned div_magic;     // ceil(2^32 / S): v = umulhi(pos, magic) for pos < 2^16 (radix path)
     int hist_shift;         // seed histogram: bin = rank >> hist_shift
     int sort;               // SortKind
+    int wide;               // 1: footprint box wider than 256: 32-bit omnigram entries and positions
     unsigned long long* phase_clock;  // optional: 8 clock64() stamps per tile (diagnostics)
     int phase_tiles;                  // capacity of phase_clock in tiles
-    // dynamic shared memory layout (byte offsets)
-    int off_vtab, off_htab, off_spans, off_frow;  // tables (whole kernel)
-    int off_om;                                    // omnigram, N x u16 (from the sort on)
-    int off_bins;                                  // counting sorts: bins
-    int off_keys, off_a, off_b, off_hist;          // radix sort: keys, ping-pong lists, histograms
-    int off_ord, off_med, off_shist;               // solve: ordinal image, medians, seed histograms
+    // Array placement. A location >= 0 is a byte offset into dynamic shared memory; a location
+    // < 0 is -(offset + 1) into the CTA's slice of global scratch.
+    int off_vtab, off_htab, off_spans, off_frow;   // tables (shared memory, whole kernel)
+    int loc_om;                                     // omnigram (from the end of the sort on)
+    int loc_bins;                                   // counting sorts: bins
+    int loc_keys, loc_a, loc_b, loc_hist;           // radix sort: keys, ping-pong lists, histograms
+    int loc_ord, loc_med, loc_shist;                // solve: ordinal image, medians, seed histograms
     int smem_bytes;
+    long long scratch_per_cta;  // bytes of global scratch per resident CTA (multiple of 256)
+    // persistent grid
+    int ntiles;                 // tiles_x * tiles_y
+    unsigned char* scratch;     // header (256 B: tile counter) + grid * scratch_per_cta
     // tables (copied to shared memory at kernel start)
     int frow[kMaxSide];                   // footprint row v covers u in [lo, hi]: lo | hi << 16
     int vtab[2 * kMaxExtent];             // per column j: top*SP + dx, (bot+1)*SP + dx
     int htab[2 * kMaxExtent];             // per row i: dy*SP + lo, dy*SP + hi + 1
     int spans[kMaxExtent];                // per row i: (lo & 0xffff) | (hi << 16)
+};
+
+// Arguments of the batched persistent launch (plans live in device memory).
+struct BatchArgs {
+    const Plan* plans;          // njobs plans, device memory
+    const int* prefix;          // njobs + 1 tile prefix sums, device memory
+    int njobs;
+    int total_tiles;
+    unsigned char* scratch;     // header (256 B: tile counter) + grid * scratch_per_cta
+    long long scratch_per_cta;
 };
 
 }  // namespace fim
@@ -89,16 +108,29 @@ struct fim_kernel {
 namespace fim {
 
 // Host-side planning (fim_host.cu).
-fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, Plan* p);
-fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts);
+fim_status get_scratch(cudaStream_t stream, size_t bytes, unsigned char** out);
+fim_status release_scratch();
+int device_sm_count();
+fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, int smem_limit,
+                     Plan* p, int cta_threads = 0);
+fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int cta_threads = 0);
 int device_smem_limit();
+
+// Autotuner cache (fim_tune.cu).
+bool tuned_lookup(const fim_kernel* k, int dtype, TileShape* ts, int cta_threads = 0);
+void tuned_store(const fim_kernel* k, int dtype, const TileShape& ts, int cta_threads = 0);
+void tuned_clear();
+void tile_candidates(std::vector<TileShape>* out);
 
 // Diagnostics: device buffer that receives per-phase clock64() stamps (may be null).
 void set_phase_clock_buffer(unsigned long long* buf, int tiles);
 void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 
 // Device launch (fim_tile.cu).
-fim_status launch_tile_kernel(const Plan& p, cudaStream_t stream);
+fim_status launch_tile_kernel(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_device_status(cudaStream_t stream);
+fim_status batch_prepare(Plan* plans, int n, int* smem_max, int* threads_max);
+fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);
+fim_status batch_launch(const BatchArgs& a, int grid, int threads, int smem, cudaStream_t stream);
 
 }  // namespace fim

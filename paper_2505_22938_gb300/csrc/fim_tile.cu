@@ -1,6 +1,7 @@
-// Per-tile median kernel: one CTA filters one Tx x Ty output tile (Sec. 3.3, Sec. 4.2).
+// Per-tile median kernel: each CTA takes Tx x Ty output tiles from a device-side queue and
+// filters them one after the other (Sec. 3.3, Sec. 4.2).
 //
-// Phases, separated by __syncthreads():
+// Phases of one tile, separated by __syncthreads():
 //   1. ordinal transform - the rounded-rectangle footprint (Fig. 10) is read with clamp-to-edge
 //                        and key-value sorted by value, giving the omnigram Omega (Sec. 3.3):
 //                          8/16-bit data: counting sort over 256 / 65536 shared-memory bins, the
@@ -13,12 +14,18 @@
 //   4. seed rows       - one warp per (seed, direction) slides the window left/right; lanes
 //                        split the kernel rows and reduce the count change (Sec. 3.3 step 4).
 //   5. vertical sweep  - one thread per (column, band, direction) slides its window up or
-//                        down (Fig. 7); the warp then refines its 32 windows one at a time
-//                        by ballot scans of Omega (Sec. 4.1 refinement, Eq. 2).
+//                        down (Fig. 7) and refines it by scanning Omega itself; the last few
+//                        lanes of a warp hand their long scans to warp ballots (Sec. 4.1, Eq. 2).
 //   6. output          - out = C[m] through the omnigram: the input value at Omega[m].
 // Pivots are exact previous medians (Huang's choice, Sec. 3.1): after each solve the count
 // below the pivot is exactly the target rank, and a slide only adds the change.
+//
+// W selects the omnigram encoding: W = 0 packs a location as two int8 coordinates (footprint
+// box up to 256 x 256, Sec. 4.1); W = 1 uses two int16 coordinates for larger boxes. OG = 1
+// keeps the omnigram in the CTA's global scratch slice when shared memory cannot hold it.
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "fim_internal.h"
 
@@ -53,6 +60,32 @@ struct Traits<FIM_F32> {
     }
 };
 
+// Omnigram entry encodings (locations relative to the footprint box centre cx0, cy0).
+template <int W>
+struct Loc;
+template <>
+struct Loc<0> {
+    using E = uint16_t;    // entry
+    using Pos = uint16_t;  // bounding-box position in the radix lists
+    static constexpr int kGroup = 8;  // entries per 128-bit load
+    __device__ static E pack(int u, int v, const Plan& P) {
+        return (E)((uint32_t)(uint8_t)(int8_t)(u - P.cx0) | ((uint32_t)(uint8_t)(int8_t)(v - P.cy0) << 8));
+    }
+    __device__ static int x(uint32_t e) { return (int)(int8_t)(e & 0xffu); }
+    __device__ static int y(uint32_t e) { return (int)(int8_t)((e >> 8) & 0xffu); }
+};
+template <>
+struct Loc<1> {
+    using E = uint32_t;
+    using Pos = uint32_t;
+    static constexpr int kGroup = 4;
+    __device__ static E pack(int u, int v, const Plan& P) {
+        return (E)((uint32_t)(uint16_t)(int16_t)(u - P.cx0) | ((uint32_t)(uint16_t)(int16_t)(v - P.cy0) << 16));
+    }
+    __device__ static int x(uint32_t e) { return (int)(int16_t)(e & 0xffffu); }
+    __device__ static int y(uint32_t e) { return (int)(int16_t)(e >> 16); }
+};
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -74,60 +107,69 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, c
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
 // Diagnostics: thread 0 records clock64() at phase boundaries when a buffer is attached.
-__device__ __forceinline__ void stamp(const Plan& P, int phase) {
-    if (P.phase_clock != nullptr && threadIdx.x == 0 && (int)blockIdx.x < P.phase_tiles)
-        P.phase_clock[blockIdx.x * 8 + phase] = clock64();
+__device__ __forceinline__ void stamp(const Plan& P, int tile, int phase) {
+    if (P.phase_clock != nullptr && threadIdx.x == 0 && tile < P.phase_tiles)
+        P.phase_clock[tile * 8 + phase] = clock64();
 }
 
 __device__ __forceinline__ int span_lo(int s) { return (int)(int16_t)(s & 0xffff); }
 __device__ __forceinline__ int span_hi(int s) { return s >> 16; }
 
-__device__ __forceinline__ uint16_t pack_loc(int u, int v, const Plan& P) {
-    return (uint16_t)((uint32_t)(uint8_t)(int8_t)(u - P.cx0) | ((uint32_t)(uint8_t)(int8_t)(v - P.cy0) << 8));
-}
-
-// Region membership of one omnigram entry (Eq. 2). The entry packs the location as two
-// int8 coordinates relative to the footprint centre; (px, py) is the window centre in the
-// same frame.
-template <int SHAPE>
+// Region membership of one omnigram entry (Eq. 2); (px, py) is the window centre in the
+// entry's coordinate frame.
+template <int SHAPE, int W>
 struct Member;
 
-template <>
-struct Member<kShapeDisk> {
+template <int W>
+struct Member<kShapeDisk, W> {
     int r2;
     __device__ __forceinline__ bool operator()(uint32_t e, int px, int py) const {
-        const int dx = (int)(int8_t)(e & 0xffu) - px;
-        const int dy = (int)(int8_t)(e >> 8) - py;
+        const int dx = Loc<W>::x(e) - px;
+        const int dy = Loc<W>::y(e) - py;
         return dx * dx + dy * dy <= r2;   // Eq. 3 on the lattice
     }
 };
 
-template <>
-struct Member<kShapeSpans> {
+template <int W>
+struct Member<kShapeSpans, W> {
     const int* spans;  // shared memory, per kernel row: lo | hi << 16
     int ymin, nrows;
     __device__ __forceinline__ bool operator()(uint32_t e, int px, int py) const {
-        const int i = (int)(int8_t)(e >> 8) - py - ymin;
+        const int i = Loc<W>::y(e) - py - ymin;
         if ((unsigned)i >= (unsigned)nrows) return false;
         const int s = spans[i];
-        const int dx = (int)(int8_t)(e & 0xffu) - px;
+        const int dx = Loc<W>::x(e) - px;
         return dx >= span_lo(s) && dx <= span_hi(s);
     }
 };
 
-// Membership of the two omnigram entries packed in one 32-bit word (entry 2k in the low half,
-// entry 2k+1 in the high half). Returns bit 0 / bit 1 for the low / high entry.
-// For the disk, (x-px)^2 + (y-py)^2 <= r2 is evaluated as x^2 + y^2 - 2(x px + y py) <= R with
-// R = r2 - px^2 - py^2, using byte dot products on the packed int8 coordinates.
-template <int SHAPE>
-struct Member2;
+// Membership of the omnigram entries held in one 32-bit word, for a fixed window: bit k is
+// entry k of the word (two 16-bit entries, or one 32-bit entry).
+template <int SHAPE, int W>
+struct WordTest {
+    Member<SHAPE, W> m;
+    int px, py;
+    __device__ __forceinline__ void init(const Member<SHAPE, W>& mm, int x, int y) {
+        m = mm;
+        px = x;
+        py = y;
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t w) const {
+        if constexpr (W == 0)
+            return (uint32_t)m(w & 0xffffu, px, py) | ((uint32_t)m(w >> 16, px, py) << 1);
+        else
+            return (uint32_t)m(w, px, py);
+    }
+};
 
+// Disk with 8-bit coordinates: (x-px)^2 + (y-py)^2 <= r2 is evaluated as
+// x^2 + y^2 - 2(x px + y py) <= r2 - px^2 - py^2 with byte dot products on the packed pair.
 template <>
-struct Member2<kShapeDisk> {
+struct WordTest<kShapeDisk, 0> {
     int R;
     int plo, phi;  // (px, py, 0, 0) and (0, 0, px, py) as signed bytes
-    __device__ __forceinline__ void set(int r2, int px, int py) {
-        R = r2 - px * px - py * py;
+    __device__ __forceinline__ void init(const Member<kShapeDisk, 0>& mm, int px, int py) {
+        R = mm.r2 - px * px - py * py;
         const uint32_t b = (uint32_t)(px & 0xff) | ((uint32_t)(py & 0xff) << 8);
         plo = (int)b;
         phi = (int)(b << 16);
@@ -141,97 +183,13 @@ struct Member2<kShapeDisk> {
     }
 };
 
-template <>
-struct Member2<kShapeSpans> {
-    Member<kShapeSpans> m;
-    int px, py;
-    __device__ __forceinline__ uint32_t operator()(uint32_t w) const {
-        return (uint32_t)m(w & 0xffffu, px, py) | ((uint32_t)m(w >> 16, px, py) << 1);
-    }
-};
-
-// Exact selection, 64 omnigram entries per iteration (two per lane from one 32-bit load).
-// Same contract as ballot_select below. Entries are taken in rank order: lane l holds ranks
-// 2(k+l) and 2(k+l)+1 of the word block starting at word k.
-template <class M2>
-__device__ __forceinline__ int ballot_select64(const uint16_t* __restrict__ om, int N, int p, int c, int target,
-                                               const M2& member2) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t* om32 = reinterpret_cast<const uint32_t*>(om);
-    const int nw = (N + 1) >> 1;
-    if (c <= target) {  // the answer is at or above p
-        int need = target - c + 1;
-        for (int k = p >> 1; k < nw; k += 32) {
-            const int kk = k + lane;
-            const int e = 2 * kk;
-            uint32_t bits = kk < nw ? member2(om32[kk]) : 0u;
-            bits &= (uint32_t)(e >= p && e < N) | ((uint32_t)(e + 1 >= p && e + 1 < N) << 1);
-            const uint32_t b0 = __ballot_sync(kFull, bits & 1u);
-            const uint32_t b1 = __ballot_sync(kFull, bits & 2u);
-            const int cnt = __popc(b0) + __popc(b1);
-            if (cnt >= need) {
-                const uint32_t lt = lanemask_lt();
-                const int before = __popc(b0 & lt) + __popc(b1 & lt);
-                const int m0 = bits & 1u, m1 = (bits >> 1) & 1u;
-                const int sel = (m0 && before + 1 == need) ? 0 : ((m1 && before + m0 + 1 == need) ? 1 : -1);
-                const uint32_t hit = __ballot_sync(kFull, sel >= 0);
-                const int wl = __ffs(hit) - 1;
-                return 2 * (k + wl) + __shfl_sync(kFull, sel, wl);
-            }
-            need -= cnt;
-        }
-    } else {  // the answer is below p: walk down, the need-th member met is the answer
-        int need = c - target;
-        for (int k1 = (p - 1) >> 1; k1 >= 0; k1 -= 32) {
-            const int kk = k1 - 31 + lane;
-            const int e = 2 * kk;
-            uint32_t bits = kk >= 0 ? member2(om32[kk]) : 0u;
-            bits &= (uint32_t)(kk >= 0 && e < p) | ((uint32_t)(kk >= 0 && e + 1 < p) << 1);
-            const uint32_t b0 = __ballot_sync(kFull, bits & 1u);
-            const uint32_t b1 = __ballot_sync(kFull, bits & 2u);
-            const int cnt = __popc(b0) + __popc(b1);
-            if (cnt >= need) {
-                const uint32_t gt = ~lanemask_le();
-                const int above = __popc(b0 & gt) + __popc(b1 & gt);
-                const int m0 = bits & 1u, m1 = (bits >> 1) & 1u;
-                const int sel = (m1 && above + 1 == need) ? 1 : ((m0 && above + m1 + 1 == need) ? 0 : -1);
-                const uint32_t hit = __ballot_sync(kFull, sel >= 0);
-                const int wl = __ffs(hit) - 1;
-                return 2 * (k1 - 31 + wl) + __shfl_sync(kFull, sel, wl);
-            }
-            need -= cnt;
-        }
-    }
-    return -1;
-}
-
-#ifndef FIM_REFINE
-#define FIM_REFINE 1
-#endif
-#ifndef FIM_VREFINE
-#define FIM_VREFINE 1
-#endif
-
-template <int SHAPE>
-__device__ __forceinline__ Member2<SHAPE> make_member2(const Member<SHAPE>& m, int px, int py, int r2) {
-    Member2<SHAPE> m2;
-    if constexpr (SHAPE == kShapeDisk) {
-        m2.set(r2, px, py);
-    } else {
-        m2.m = m;
-        m2.px = px;
-        m2.py = py;
-    }
-    return m2;
-}
-
 // Exact selection by ballot scans of the omnigram (Sec. 4.1, Sec. 4.2).
 // Given a pivot rank p and c = #{window members with rank < p}, returns the rank m of the
 // window element with window-rank `target`. All 32 lanes pass the same arguments and get
 // the same result; -1 means the counts were inconsistent (never expected).
-template <class M>
-__device__ __forceinline__ int ballot_select(const uint16_t* __restrict__ om, int N, int p, int c, int target,
-                                             int px, int py, const M& member) {
+template <class E, class M>
+__device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, int p, int c, int target, int px,
+                                             int py, const M& member) {
     const int lane = threadIdx.x & 31;
     if (c <= target) {  // the answer is at or above p
         int need = target - c + 1;
@@ -264,25 +222,27 @@ __device__ __forceinline__ int ballot_select(const uint16_t* __restrict__ om, in
 }
 
 // Per-thread exact selection (vertical sweep): every lane refines its own window. It scans the
-// omnigram from its pivot in aligned groups of 8 entries (one 128-bit load), counting members
-// with the packed-pair test, until the group holding the target-th member. While at least
-// kHandoff lanes are still scanning this is the cheapest schedule; the last few lanes of a warp
-// (long jumps at edges and impulses) are finished by warp-cooperative ballot scans instead of
-// keeping 29+ lanes idle. Same contract as ballot_select, per lane. All loops are bounded by
-// the omnigram length.
+// omnigram from its pivot in aligned groups of entries (one 128-bit load), counting members,
+// until the group holding the target-th member. While at least kHandoff lanes are still
+// scanning this is the cheapest schedule; the last few lanes of a warp (long jumps at edges and
+// impulses) are finished by warp-cooperative ballot scans instead of keeping 29+ lanes idle.
+// Same contract as ballot_select, per lane. All loops are bounded by the omnigram length.
 constexpr int kHandoff = 4;
-constexpr int kHandoffAfter = 16;  // groups of 8 entries
+constexpr int kHandoffAfter = 16;  // groups
 
-template <int SHAPE>
-__device__ __forceinline__ int thread_select(const uint16_t* __restrict__ om, int N, int p, int c, int target,
-                                             int px, int py, const Member<SHAPE>& member, int r2) {
+template <int SHAPE, int W>
+__device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
+                                             int target, int px, int py, const Member<SHAPE, W>& member) {
+    constexpr int G = Loc<W>::kGroup;
+    constexpr uint32_t kAll = (1u << G) - 1;
     const int lane = threadIdx.x & 31;
-    const Member2<SHAPE> member2 = make_member2<SHAPE>(member, px, py, r2);
+    WordTest<SHAPE, W> wt;
+    wt.init(member, px, py);
     const uint4* om128 = reinterpret_cast<const uint4*>(om);
     const bool up = c <= target;
     int need = up ? target - c + 1 : c - target;
-    int nextv = up ? p : p - 1;      // next omnigram entry to examine
-    const int glast = (N - 1) >> 3;
+    int nextv = up ? p : p - 1;  // next omnigram entry to examine
+    const int glast = (N - 1) / G;
     bool done = false;
     int m = -1;
     for (int it = 0; it <= glast + 1; ++it) {
@@ -290,27 +250,29 @@ __device__ __forceinline__ int thread_select(const uint16_t* __restrict__ om, in
         if (it >= kHandoffAfter && __popc(__ballot_sync(kFull, !done)) < kHandoff) break;
         if (it < kHandoffAfter && !__any_sync(kFull, !done)) break;
         if (!done) {
-            const int g = nextv >> 3;
+            const int g = nextv >= 0 ? nextv / G : -1;
             if (g < 0 || g > glast) {
                 done = true;
             } else {
                 const uint4 q = om128[g];
-                uint32_t mask = member2(q.x) | (member2(q.y) << 2) | (member2(q.z) << 4) | (member2(q.w) << 6);
-                mask &= up ? (0xffu << (nextv & 7)) & 0xffu : (0xffu >> (7 - (nextv & 7)));
-                if (g == glast) mask &= 0xffu >> (7 - ((N - 1) & 7));
+                constexpr int kb = G / 4;  // entries per word
+                uint32_t mask = wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb));
+                const int o = nextv - g * G;
+                mask &= up ? (kAll << o) & kAll : (kAll >> (G - 1 - o));
+                if (g == glast) mask &= kAll >> (G - 1 - (N - 1 - glast * G));
                 const int cnt = __popc(mask);
                 if (cnt >= need) {
                     if (up) {
                         for (int k = 1; k < need; ++k) mask &= mask - 1;  // drop the lowest need-1
-                        m = 8 * g + __ffs(mask) - 1;
+                        m = G * g + __ffs(mask) - 1;
                     } else {
                         for (int k = 1; k < need; ++k) mask ^= 1u << (31 - __clz(mask));  // drop the highest
-                        m = 8 * g + 31 - __clz(mask);
+                        m = G * g + 31 - __clz(mask);
                     }
                     done = true;
                 } else {
                     need -= cnt;
-                    nextv = up ? 8 * g + 8 : 8 * g - 1;
+                    nextv = up ? G * g + G : G * g - 1;
                 }
             }
         }
@@ -330,17 +292,6 @@ __device__ __forceinline__ int thread_select(const uint16_t* __restrict__ om, in
         if (lane == j) m = mj;
     }
     return m;
-}
-
-// Refinement entry point used by every phase: exact rank of the target-th window member.
-template <int SHAPE>
-__device__ __forceinline__ int refine(const uint16_t* __restrict__ om, int N, int p, int c, int target, int px,
-                                      int py, const Member<SHAPE>& member, int r2) {
-#if FIM_REFINE == 1
-    return ballot_select(om, N, p, c, target, px, py, member);
-#else
-    return ballot_select64(om, N, p, c, target, make_member2<SHAPE>(member, px, py, r2));
-#endif
 }
 
 // Block-wide exclusive scan of 65536 16-bit counters packed two per word (bin 2k in the low
@@ -390,6 +341,7 @@ __device__ void scan_bins16(uint32_t* bins, const Plan& P) {
         b4[it * 32 + lane] = make_uint4(w[0], w[1], w[2], w[3]);
         run += __shfl_sync(kFull, incl, 31);
     }
+    __syncthreads();
 }
 
 template <int DT>
@@ -402,11 +354,10 @@ __device__ __forceinline__ typename Traits<DT>::T load_px(const char* in, const 
 // Counting-sort ordinal transform for 8/16-bit data (Sec. 4.1, Eq. 5): histogram of the
 // footprint, exclusive prefix, then every pixel takes the next free ordinal of its value.
 // Ties get consecutive ordinals in arrival order, which is all the method needs.
-template <int DT>
-__device__ void ordinal_transform_count(const Plan& P, const int* frow, uint16_t* om, int gx0, int gy0) {
-    extern __shared__ __align__(16) unsigned char smem[];
+template <int DT, int W>
+__device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t* bins, typename Loc<W>::E* om,
+                                        int gx0, int gy0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t* bins = reinterpret_cast<uint32_t*>(smem + P.off_bins);
     const char* in = static_cast<const char*>(P.in);
     constexpr bool k16 = DT == FIM_U16;
     const int nwords = k16 ? 32768 : 256;
@@ -426,26 +377,28 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint16_t
     __syncthreads();
     if (k16) {
         scan_bins16(bins, P);
-    } else if (warp == 0) {
-        uint32_t c[8], s = 0;
+    } else {
+        if (warp == 0) {
+            uint32_t c[8], s = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            c[k] = bins[lane * 8 + k];
-            s += c[k];
-        }
-        uint32_t incl = s;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        uint32_t b = incl - s;
+            for (int k = 0; k < 8; ++k) {
+                c[k] = bins[lane * 8 + k];
+                s += c[k];
+            }
+            uint32_t incl = s;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t b = incl - s;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            bins[lane * 8 + k] = b;
-            b += c[k];
+            for (int k = 0; k < 8; ++k) {
+                bins[lane * 8 + k] = b;
+                b += c[k];
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int v = warp; v < P.SH; v += P.nwarps) {
         const int fr = frow[v];
         for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
@@ -457,7 +410,7 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint16_t
             } else {
                 o = atomicAdd(&bins[key], 1u);
             }
-            om[o] = pack_loc(u, v, P);
+            om[o] = Loc<W>::pack(u, v, P);
         }
     }
 }
@@ -466,18 +419,16 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint16_t
 // bounding-box positions. Each warp owns one contiguous segment of the current order; a
 // pixel's new place is its (digit, warp)-major exclusive offset plus its position among
 // equal digits earlier in the segment (warp match). Histograms are laid out warp-major with
-// a pad word so that the leaders of one warp never share a bank.
-template <int DT>
-__device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint16_t* om, int gx0, int gy0) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// a pad word so that the leaders of one warp never share a bank. The sorted positions end in
+// list B, which is then rewritten in place as the omnigram.
+template <int DT, int W>
+__device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t* keys, typename Loc<W>::Pos* bufA,
+                                        typename Loc<W>::Pos* bufB, uint32_t* hist, int gx0, int gy0) {
+    using Pos = typename Loc<W>::Pos;
     __shared__ uint32_t wsum[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
     constexpr int HS = kSortBins + 1;
-    uint32_t* keys = reinterpret_cast<uint32_t*>(smem + P.off_keys);
-    uint16_t* bufA = reinterpret_cast<uint16_t*>(smem + P.off_a);
-    uint16_t* bufB = reinterpret_cast<uint16_t*>(smem + P.off_b);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + P.off_hist);
     const char* in = static_cast<const char*>(P.in);
     for (int v = warp; v < P.SH; v += nwarps) {
         const int fr = frow[v];
@@ -486,8 +437,8 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint16_t
     }
     __syncthreads();
     const int area = S * P.SH;
-    const uint16_t* src = nullptr;
-    uint16_t* dst = bufA;
+    const Pos* src = nullptr;
+    Pos* dst = bufA;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         const int len = pass == 0 ? area : P.N;
@@ -508,7 +459,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint16_t
                     valid = u >= span_lo(fr) && u <= span_hi(fr);
                     pos = i;
                 } else {
-                    pos = src[i];
+                    pos = (int)src[i];
                 }
             }
             const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
@@ -565,7 +516,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint16_t
                     valid = u >= span_lo(fr) && u <= span_hi(fr);
                     pos = i;
                 } else {
-                    pos = src[i];
+                    pos = (int)src[i];
                 }
             }
             const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
@@ -574,7 +525,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint16_t
             if (valid) base = hw[d];
             __syncwarp();
             if (valid) {
-                dst[base + __popc(peers & lanemask_lt())] = (uint16_t)pos;
+                dst[base + __popc(peers & lanemask_lt())] = (Pos)pos;
                 if (lane == __ffs(peers) - 1) hw[d] = base + __popc(peers);
             }
             __syncwarp();
@@ -583,68 +534,67 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint16_t
         src = dst;
         dst = (dst == bufA) ? bufB : bufA;
     }
-    // four passes: the sorted positions are in B; the omnigram goes to A
+    // four passes: the sorted positions are in B; rewrite them in place as omnigram entries
+    typename Loc<W>::E* om = reinterpret_cast<typename Loc<W>::E*>(bufB);
     for (int v = tid; v < P.N; v += nthreads) {
-        const int pos = src[v];
+        const int pos = (int)bufB[v];
         const int y = (int)__umulhi((unsigned)pos, P.div_magic);
-        om[v] = pack_loc(pos - y * S, y, P);
+        om[v] = Loc<W>::pack(pos - y * S, y, P);
     }
 }
 
-template <int DT, int SHAPE>
-__global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_constant__ Plan P) {
-    using V = typename Traits<DT>::T;
-    extern __shared__ __align__(16) unsigned char smem[];
+template <class T>
+__device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, int loc) {
+    return reinterpret_cast<T*>(loc >= 0 ? smem + loc : gslice + (-(long long)loc - 1));
+}
 
+template <int DT, int SHAPE, int W, int OG>
+__device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using V = typename Traits<DT>::T;
+    using E = typename Loc<W>::E;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const int nthreads = P.threads;
     const int nwarps = P.nwarps;
     const int SP = P.SP, N = P.N, TX = P.Tx, TY = P.Ty;
-    const int tile = blockIdx.x;
     const int tx0 = (tile % P.tiles_x) * TX;
     const int ty0 = (tile / P.tiles_x) * TY;
     const int gx0 = tx0 + P.xmin;  // global coordinates of bounding-box pixel (0, 0)
     const int gy0 = ty0 + P.ymin;
 
-    int2* vtab = reinterpret_cast<int2*>(smem + P.off_vtab);
-    int2* htab = reinterpret_cast<int2*>(smem + P.off_htab);
-    int* spans = reinterpret_cast<int*>(smem + P.off_spans);
-    int* frow = reinterpret_cast<int*>(smem + P.off_frow);
-    uint16_t* om = reinterpret_cast<uint16_t*>(smem + P.off_om);
-    uint16_t* ord = reinterpret_cast<uint16_t*>(smem + P.off_ord);
-    uint16_t* med = reinterpret_cast<uint16_t*>(smem + P.off_med);
-    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + P.off_shist);
-
-    stamp(P, 0);
-    for (int i = tid; i < P.ncols; i += nthreads) vtab[i] = make_int2(P.vtab[2 * i], P.vtab[2 * i + 1]);
-    for (int i = tid; i < P.nrows; i += nthreads) {
-        htab[i] = make_int2(P.htab[2 * i], P.htab[2 * i + 1]);
-        spans[i] = P.spans[i];
-    }
-    for (int i = tid; i < P.SH; i += nthreads) frow[i] = P.frow[i];
-    __syncthreads();
+    const int2* vtab = reinterpret_cast<const int2*>(smem + P.off_vtab);
+    const int2* htab = reinterpret_cast<const int2*>(smem + P.off_htab);
+    const int* spans = reinterpret_cast<const int*>(smem + P.off_spans);
+    const int* frow = reinterpret_cast<const int*>(smem + P.off_frow);
+    // The omnigram's home is fixed per instantiation (OG), so the compiler keeps shared-memory
+    // accesses as such; everything else of the solve always lives in shared memory.
+    E* om = OG ? reinterpret_cast<E*>(gslice + (-(long long)P.loc_om - 1)) : reinterpret_cast<E*>(smem + P.loc_om);
+    uint16_t* ord = reinterpret_cast<uint16_t*>(smem + P.loc_ord);
+    uint16_t* med = reinterpret_cast<uint16_t*>(smem + P.loc_med);
+    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + P.loc_shist);
 
     // ---- 1. ordinal transform ------------------------------------------------------------------
-    stamp(P, 1);
+    stamp(P, tile, 1);
     if constexpr (DT == FIM_F32)
-        ordinal_transform_radix<DT>(P, frow, om, gx0, gy0);
+        ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
+                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
+                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
+                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), gx0, gy0);
     else
-        ordinal_transform_count<DT>(P, frow, om, gx0, gy0);
+        ordinal_transform_count<DT, W>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), om, gx0, gy0);
     __syncthreads();
 
     // ---- 2. ordinal image I (Eq. 4) ------------------------------------------------------------
-    stamp(P, 2);
+    stamp(P, tile, 2);
     for (int v = tid; v < N; v += nthreads) {
         const uint32_t e = om[v];
-        const int u = (int)(int8_t)(e & 0xffu) + P.cx0;
-        const int y = (int)(int8_t)(e >> 8) + P.cy0;
-        ord[y * SP + u] = (uint16_t)v;
+        ord[(Loc<W>::y(e) + P.cy0) * SP + Loc<W>::x(e) + P.cx0] = (uint16_t)v;
     }
     __syncthreads();
 
-    Member<SHAPE> member;
+    Member<SHAPE, W> member;
     if constexpr (SHAPE == kShapeDisk) {
         member.r2 = P.r2;
     } else {
@@ -657,12 +607,13 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
     const int GW = TX / P.G;       // seed spacing within a seed row
 
     // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
-    stamp(P, 3);
+    stamp(P, tile, 3);
     for (int sd = warp; sd < P.RB * P.G; sd += nwarps) {
         const int band = sd / P.G, g = sd % P.G;
         const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
         const int cu = s - P.xmin, cv = t - P.ymin;             // window centre in the box
-        uint32_t* hw = shist + warp * kSeedBins;
+        // one histogram per concurrently solved seed
+        uint32_t* hw = shist + (nwarps >= P.RB * P.G ? sd : warp) * kSeedBins;
         for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
         __syncwarp();
         // Lane l takes kernel rows l, l+32, ... and walks each from a lane-dependent column,
@@ -703,7 +654,7 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
         const int src_lane = __ffs(who) - 1;
         bin = __shfl_sync(kFull, bin, src_lane);
         below = __shfl_sync(kFull, below, src_lane);
-        const int m = refine<SHAPE>(om, N, bin << P.hist_shift, below, target, cu - P.cx0, cv - P.cy0, member, P.r2);
+        const int m = ballot_select(om, N, bin << P.hist_shift, below, target, cu - P.cx0, cv - P.cy0, member);
         if (m < 0) set_status(FIM_ERR_INTERNAL);
         if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
         __syncwarp();
@@ -711,7 +662,7 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
     __syncthreads();
 
     // ---- 4. seed rows: horizontal slides, lanes split the kernel rows ----------------------
-    stamp(P, 4);
+    stamp(P, tile, 4);
     for (int job = warp; job < 2 * P.RB * P.G; job += nwarps) {
         const int sd = job >> 1, right = job & 1;
         const int band = sd / P.G, g = sd % P.G;
@@ -733,7 +684,7 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
             d = __reduce_add_sync(kFull, d);
             cu += right ? 1 : -1;
             s += right ? 1 : -1;
-            const int m = refine<SHAPE>(om, N, p, target + d, target, cu - P.cx0, cv - P.cy0, member, P.r2);
+            const int m = ballot_select(om, N, p, target + d, target, cu - P.cx0, cv - P.cy0, member);
             if (m < 0) set_status(FIM_ERR_INTERNAL);
             p = max(m, 0);
             if (lane == 0) med[t * TX + s] = (uint16_t)p;
@@ -741,9 +692,9 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
     }
     __syncthreads();
 
-    // ---- 5. vertical sweeps: thread per window column, warp-cooperative refinement ----------
-    stamp(P, 5);
-    {
+    // ---- 5. vertical sweeps: thread per window column, per-thread refinement ----------------
+    stamp(P, tile, 5);
+    if (warp < P.vthreads / 32) {
         const int groups = TX / 32;
         const int cg = warp % groups;
         const int rest = warp / groups;
@@ -775,18 +726,7 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
             }
             cv += down ? 1 : -1;
             t += down ? 1 : -1;
-            const int c = target + d;
-#if FIM_VREFINE == 0
-            int mine = 0;
-            for (int j = 0; j < 32; ++j) {
-                const int pj = __shfl_sync(kFull, p, j);
-                const int cj = __shfl_sync(kFull, c, j);
-                const int m = refine<SHAPE>(om, N, pj, cj, target, cu - lane + j - P.cx0, cv - P.cy0, member, P.r2);
-                if (lane == j) mine = m;
-            }
-#else
-            const int mine = thread_select<SHAPE>(om, N, p, c, target, cu - P.cx0, cv - P.cy0, member, P.r2);
-#endif
+            const int mine = thread_select<SHAPE, W>(om, N, p, target + d, target, cu - P.cx0, cv - P.cy0, member);
             if (mine < 0) set_status(FIM_ERR_INTERNAL);
             p = max(mine, 0);
             med[t * TX + s] = (uint16_t)p;
@@ -795,7 +735,7 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
     __syncthreads();
 
     // ---- 6. output: the input value at Omega[m] ------------------------------------------------
-    stamp(P, 6);
+    stamp(P, tile, 6);
     const char* in = static_cast<const char*>(P.in);
     char* out = static_cast<char*>(P.out);
     for (int idx = tid; idx < TX * TY; idx += nthreads) {
@@ -803,39 +743,189 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
         const int gx = tx0 + s, gy = ty0 + t;
         if (gx >= P.w || gy >= P.h) continue;
         const uint32_t e = om[med[idx]];
-        const int u = (int)(int8_t)(e & 0xffu) + P.cx0;
-        const int v = (int)(int8_t)(e >> 8) + P.cy0;
-        const V val = load_px<DT>(in, P, gx0 + u, gy0 + v);
+        const V val = load_px<DT>(in, P, gx0 + Loc<W>::x(e) + P.cx0, gy0 + Loc<W>::y(e) + P.cy0);
         reinterpret_cast<V*>(out + (long long)gy * P.pitch)[gx] = val;
     }
     __syncthreads();
-    stamp(P, 7);
+    stamp(P, tile, 7);
 }
 
-template <int DT, int SHAPE>
-fim_status launch_typed(const Plan& p, cudaStream_t stream) {
-    auto fn = tile_median_kernel<DT, SHAPE>;
+__device__ __forceinline__ void load_tables(const Plan& P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int2* vtab = reinterpret_cast<int2*>(smem + P.off_vtab);
+    int2* htab = reinterpret_cast<int2*>(smem + P.off_htab);
+    int* spans = reinterpret_cast<int*>(smem + P.off_spans);
+    int* frow = reinterpret_cast<int*>(smem + P.off_frow);
+    for (int i = tid; i < P.ncols; i += nt) vtab[i] = make_int2(P.vtab[2 * i], P.vtab[2 * i + 1]);
+    for (int i = tid; i < P.nrows; i += nt) {
+        htab[i] = make_int2(P.htab[2 * i], P.htab[2 * i + 1]);
+        spans[i] = P.spans[i];
+    }
+    for (int i = tid; i < P.SH; i += nt) frow[i] = P.frow[i];
+}
+
+// Persistent CTAs: each takes tiles from the queue counter in the scratch header until none are
+// left. The counter is zeroed on the stream before every launch.
+template <int DT, int SHAPE, int W, int OG>
+__global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_constant__ Plan P) {
+    __shared__ int s_tile;
+    const int tid = threadIdx.x;
+    unsigned char* gslice = P.scratch + 256 + (size_t)blockIdx.x * (size_t)P.scratch_per_cta;
+    load_tables(P);
+    unsigned int* counter = reinterpret_cast<unsigned int*>(P.scratch);
+    for (;;) {
+        if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= P.ntiles) break;
+        stamp(P, tile, 0);
+        process_tile<DT, SHAPE, W, OG>(P, tile, gslice);
+    }
+}
+
+// ---- batched persistent launch ---------------------------------------------------------------
+// One queue of tiles spans every job of a batch (jobs sorted by decreasing cost per tile on the
+// host, so the long tiles start first). A CTA maps a queue index to (job, tile) through the
+// prefix table, loads the job's tables into shared memory when its job changes, and runs the
+// job's instantiation of the tile pipeline.
+template <int DT, int SHAPE, int W, int OG>
+__device__ __noinline__ void batch_tile(const Plan* P, int tile, unsigned char* gslice) {
+    process_tile<DT, SHAPE, W, OG>(*P, tile, gslice);
+}
+
+__device__ void dispatch_tile(const Plan* P, int tile, unsigned char* gslice) {
+    const int cls = P->wide ? 2 : (P->loc_om < 0 ? 1 : 0);
+    const bool disk = P->shape == kShapeDisk;
+#define FIM_CASE(DT)                                                                   \
+    if (disk) {                                                                        \
+        if (cls == 0) batch_tile<DT, kShapeDisk, 0, 0>(P, tile, gslice);              \
+        else if (cls == 1) batch_tile<DT, kShapeDisk, 0, 1>(P, tile, gslice);         \
+        else batch_tile<DT, kShapeDisk, 1, 1>(P, tile, gslice);                       \
+    } else {                                                                           \
+        if (cls == 0) batch_tile<DT, kShapeSpans, 0, 0>(P, tile, gslice);             \
+        else if (cls == 1) batch_tile<DT, kShapeSpans, 0, 1>(P, tile, gslice);        \
+        else batch_tile<DT, kShapeSpans, 1, 1>(P, tile, gslice);                      \
+    }
+    switch (P->dtype) {
+        case FIM_U8: FIM_CASE(FIM_U8) break;
+        case FIM_U16: FIM_CASE(FIM_U16) break;
+        default: FIM_CASE(FIM_F32) break;
+    }
+#undef FIM_CASE
+}
+
+__global__ void __launch_bounds__(1024, 1) batch_median_kernel(const __grid_constant__ BatchArgs A) {
+    __shared__ int s_tile, s_job;
+    const int tid = threadIdx.x;
+    unsigned char* gslice = A.scratch + 256 + (size_t)blockIdx.x * (size_t)A.scratch_per_cta;
+    unsigned int* counter = reinterpret_cast<unsigned int*>(A.scratch);
+    int cur = -1;
+    for (;;) {
+        if (tid == 0) {
+            const int t = (int)atomicAdd(counter, 1u);
+            int j = -1;
+            if (t < A.total_tiles) {  // binary search: prefix[j] <= t < prefix[j + 1]
+                int lo = 0, hi = A.njobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (A.prefix[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                j = lo;
+            }
+            s_tile = t;
+            s_job = j;
+        }
+        __syncthreads();
+        const int job = s_job;
+        const int t = s_tile;
+        if (job < 0) break;
+        const Plan* P = A.plans + job;
+        if (job != cur) {
+            load_tables(*P);
+            __syncthreads();
+            cur = job;
+        }
+        dispatch_tile(P, t - A.prefix[job], gslice);  // every plan of a batch has this CTA size
+        __syncthreads();
+    }
+}
+
+template <int DT, int SHAPE, int W, int OG>
+fim_status launch_typed(Plan& p, cudaStream_t stream) {
+    auto fn = tile_median_kernel<DT, SHAPE, W, OG>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes) != cudaSuccess) {
         cudaGetLastError();
         return FIM_ERR_CUDA;
     }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p.threads, p.smem_bytes) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return FIM_ERR_UNSUPPORTED;
+    }
     const long long tiles = (long long)p.tiles_x * p.tiles_y;
     if (tiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
-    fn<<<(unsigned)tiles, p.threads, p.smem_bytes, stream>>>(p);
+    p.ntiles = (int)tiles;
+    const int grid = (int)std::min<long long>(tiles, (long long)occ * device_sm_count());
+    unsigned char* scratch = nullptr;
+    fim_status s = get_scratch(stream, 256 + (size_t)grid * (size_t)p.scratch_per_cta, &scratch);
+    if (s != FIM_OK) return s;
+    p.scratch = scratch;
+    if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;
+    fn<<<grid, p.threads, p.smem_bytes, stream>>>(p);
     if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;
     return FIM_OK;
 }
 
+template <int DT, int SHAPE>
+fim_status launch_w(Plan& p, cudaStream_t stream) {
+    if (p.wide) return launch_typed<DT, SHAPE, 1, 1>(p, stream);
+    return p.loc_om < 0 ? launch_typed<DT, SHAPE, 0, 1>(p, stream) : launch_typed<DT, SHAPE, 0, 0>(p, stream);
+}
+
 }  // namespace
 
-fim_status launch_tile_kernel(const Plan& p, cudaStream_t stream) {
+fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
     const bool disk = p.shape == kShapeDisk;
     switch (p.dtype) {
-        case FIM_U8: return disk ? launch_typed<FIM_U8, kShapeDisk>(p, stream) : launch_typed<FIM_U8, kShapeSpans>(p, stream);
-        case FIM_U16: return disk ? launch_typed<FIM_U16, kShapeDisk>(p, stream) : launch_typed<FIM_U16, kShapeSpans>(p, stream);
-        case FIM_F32: return disk ? launch_typed<FIM_F32, kShapeDisk>(p, stream) : launch_typed<FIM_F32, kShapeSpans>(p, stream);
+        case FIM_U8: return disk ? launch_w<FIM_U8, kShapeDisk>(p, stream) : launch_w<FIM_U8, kShapeSpans>(p, stream);
+        case FIM_U16: return disk ? launch_w<FIM_U16, kShapeDisk>(p, stream) : launch_w<FIM_U16, kShapeSpans>(p, stream);
+        case FIM_F32: return disk ? launch_w<FIM_F32, kShapeDisk>(p, stream) : launch_w<FIM_F32, kShapeSpans>(p, stream);
     }
     return FIM_ERR_INVALID_ARG;
+}
+
+fim_status batch_prepare(Plan* plans, int n, int* smem_max, int* threads_max) {
+    int smem = 0, thr = 32;
+    for (int i = 0; i < n; ++i) {
+        smem = std::max(smem, plans[i].smem_bytes);
+        thr = std::max(thr, plans[i].threads);
+    }
+    if (cudaFuncSetAttribute(batch_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return FIM_ERR_CUDA;
+    }
+    *smem_max = smem;
+    *threads_max = thr;
+    return FIM_OK;
+}
+
+fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_median_kernel, threads, smem) != cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        return FIM_ERR_UNSUPPORTED;
+    }
+    *grid = (int)std::min<long long>(total_tiles, (long long)occ * device_sm_count());
+    return FIM_OK;
+}
+
+fim_status batch_launch(const BatchArgs& a, int grid, int threads, int smem, cudaStream_t stream) {
+    if (cudaMemsetAsync(a.scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;
+    batch_median_kernel<<<grid, threads, smem, stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;
+    return FIM_OK;
 }
 
 fim_status read_and_clear_device_status(cudaStream_t stream) {

@@ -142,3 +142,48 @@ def test_full_size_config2_sampled():
         got = to_host(out)[ys, xs]
         exp = oracle.median_points(img, oracle.disk_offsets(r), xs, ys)
         assert np.array_equal(got, exp), f"r={r}: {np.sum(got != exp)} of {len(xs)} samples differ"
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+@pytest.mark.parametrize("r", [100, 113, 128])
+def test_large_radius(dtype, r):
+    """Kernels whose footprint needs global scratch (radix keys, 32-bit omnigram entries)."""
+    img = datagen.image_for(dtype, 500 + r, 45, 71)
+    run_case(img, "circle", r)
+
+
+def test_f32_r100_multi_tile():
+    img = datagen.image_for("f32", 601, 70, 99)
+    run_case(img, "circle", 100)
+
+
+@pytest.mark.parametrize("spec", [("ellipse", 128, 20), ("ellipse", 20, 128), ("disk_limit", 128 * 128 + 128)])
+def test_large_extents(spec):
+    img = datagen.image_for("u16", 602, 40, 44)
+    run_case(img, *spec)
+
+
+def test_full_size_config3_sampled():
+    """8192x8192 f32 (fields + Cauchy outliers) at disk r=64 and 100, the hexagon (R=64) and
+    the 80x40 ellipse, in the launch configuration of a full-image call: sampled pixels,
+    including tile and image borders, against the oracle point by point."""
+    import torch
+    import paper_2505_22938_gb300 as fim
+    img = datagen.config3_image()
+    rng = np.random.default_rng(3)
+    n = 600
+    xs = np.concatenate([rng.integers(0, 8192, n), [0, 8191, 31, 32, 63, 64, 8160, 8191, 0]])
+    ys = np.concatenate([rng.integers(0, 8192, n), [8191, 0, 32, 31, 64, 63, 8191, 8160, 4095]])
+    dev = torch.from_numpy(img).cuda()
+    out = torch.empty_like(dev)
+    cases = [("circle", 64), ("circle", 100), ("polygon", oracle.regular_polygon_vertices(6, 64.0)),
+             ("ellipse", 80, 40)]
+    for spec in cases:
+        k = fim_kernel(*spec)
+        fim.median(dev, k, out=out)
+        torch.cuda.synchronize()
+        assert fim.fim_sync_status() == 0
+        got = out.cpu().numpy()[ys, xs]
+        exp = oracle.median_points(img, oracle_offsets(*spec), xs, ys)
+        assert np.array_equal(got.view(np.uint32), exp.view(np.uint32)), \
+            f"{spec[0]}: {np.sum(got.view(np.uint32) != exp.view(np.uint32))} of {len(xs)} samples differ"
