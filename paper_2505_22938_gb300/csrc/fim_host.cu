@@ -163,7 +163,7 @@ int device_smem_limit() {
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-    return v;
+    return v - 1024;  // dynamic shared memory; the kernels' static shared variables need the rest
 }
 
 static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <map>
@@ -82,6 +83,11 @@ struct Plan {
     int htab[2 * kMaxExtent];             // per row i: dy*SP + lo, dy*SP + hi + 1
     int spans[kMaxExtent];                // per row i: (lo & 0xffff) | (hi << 16)
 };
+
+// Bytes of a Plan before its tables: all the tile pipeline reads once the tables are in
+// shared memory.
+constexpr size_t kPlanScalarBytes = ((offsetof(Plan, frow) + 15) / 16) * 16;
+static_assert(offsetof(Plan, frow) % 4 == 0, "plan scalars are copied as 32-bit words");
 
 // Arguments of the batched persistent launch (plans live in device memory).
 struct BatchArgs {

@@ -68,8 +68,8 @@ struct Loc<0> {
     using E = uint16_t;    // entry
     using Pos = uint16_t;  // bounding-box position in the radix lists
     static constexpr int kGroup = 8;  // entries per 128-bit load
-    __device__ static E pack(int u, int v, const Plan& P) {
-        return (E)((uint32_t)(uint8_t)(int8_t)(u - P.cx0) | ((uint32_t)(uint8_t)(int8_t)(v - P.cy0) << 8));
+    __device__ static E pack(int u, int v, int cx0, int cy0) {
+        return (E)((uint32_t)(uint8_t)(int8_t)(u - cx0) | ((uint32_t)(uint8_t)(int8_t)(v - cy0) << 8));
     }
     __device__ static int x(uint32_t e) { return (int)(int8_t)(e & 0xffu); }
     __device__ static int y(uint32_t e) { return (int)(int8_t)((e >> 8) & 0xffu); }
@@ -79,8 +79,8 @@ struct Loc<1> {
     using E = uint32_t;
     using Pos = uint32_t;
     static constexpr int kGroup = 4;
-    __device__ static E pack(int u, int v, const Plan& P) {
-        return (E)((uint32_t)(uint16_t)(int16_t)(u - P.cx0) | ((uint32_t)(uint16_t)(int16_t)(v - P.cy0) << 16));
+    __device__ static E pack(int u, int v, int cx0, int cy0) {
+        return (E)((uint32_t)(uint16_t)(int16_t)(u - cx0) | ((uint32_t)(uint16_t)(int16_t)(v - cy0) << 16));
     }
     __device__ static int x(uint32_t e) { return (int)(int16_t)(e & 0xffffu); }
     __device__ static int y(uint32_t e) { return (int)(int16_t)(e >> 16); }
@@ -344,11 +344,20 @@ __device__ void scan_bins16(uint32_t* bins, const Plan& P) {
     __syncthreads();
 }
 
+// The image as the tile pipeline reads it, held in registers.
+struct Img {
+    const char* in;
+    long long pitch;
+    int w, h;
+    __device__ __forceinline__ explicit Img(const Plan& P)
+        : in(static_cast<const char*>(P.in)), pitch(P.pitch), w(P.w), h(P.h) {}
+};
+
 template <int DT>
-__device__ __forceinline__ typename Traits<DT>::T load_px(const char* in, const Plan& P, int gx, int gy) {
+__device__ __forceinline__ typename Traits<DT>::T load_px(const Img& im, int gx, int gy) {
     using V = typename Traits<DT>::T;
-    const V* row = reinterpret_cast<const V*>(in + (long long)clampi(gy, 0, P.h - 1) * P.pitch);
-    return __ldg(row + clampi(gx, 0, P.w - 1));
+    const V* row = reinterpret_cast<const V*>(im.in + (long long)clampi(gy, 0, im.h - 1) * im.pitch);
+    return __ldg(row + clampi(gx, 0, im.w - 1));
 }
 
 // Counting-sort ordinal transform for 8/16-bit data (Sec. 4.1, Eq. 5): histogram of the
@@ -358,16 +367,17 @@ template <int DT, int W>
 __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t* bins, typename Loc<W>::E* om,
                                         int gx0, int gy0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const char* in = static_cast<const char*>(P.in);
+    const Img im(P);
+    const int SH = P.SH, nwarps = P.nwarps, cx0 = P.cx0, cy0 = P.cy0;
     constexpr bool k16 = DT == FIM_U16;
     const int nwords = k16 ? 32768 : 256;
     for (int i = tid * 4; i < nwords; i += P.threads * 4)
         *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    for (int v = warp; v < P.SH; v += P.nwarps) {
+    for (int v = warp; v < SH; v += nwarps) {
         const int fr = frow[v];
         for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
-            const uint32_t key = Traits<DT>::key(load_px<DT>(in, P, gx0 + u, gy0 + v));
+            const uint32_t key = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
             if (k16)
                 atomicAdd(&bins[key >> 1], 1u << ((key & 1u) << 4));
             else
@@ -399,10 +409,10 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
         }
         __syncthreads();
     }
-    for (int v = warp; v < P.SH; v += P.nwarps) {
+    for (int v = warp; v < SH; v += nwarps) {
         const int fr = frow[v];
         for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
-            const uint32_t key = Traits<DT>::key(load_px<DT>(in, P, gx0 + u, gy0 + v));
+            const uint32_t key = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
             uint32_t o;
             if (k16) {
                 const uint32_t sh = (key & 1u) << 4;
@@ -410,7 +420,7 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
             } else {
                 o = atomicAdd(&bins[key], 1u);
             }
-            om[o] = Loc<W>::pack(u, v, P);
+            om[o] = Loc<W>::pack(u, v, cx0, cy0);
         }
     }
 }
@@ -429,11 +439,11 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
     constexpr int HS = kSortBins + 1;
-    const char* in = static_cast<const char*>(P.in);
+    const Img im(P);
     for (int v = warp; v < P.SH; v += nwarps) {
         const int fr = frow[v];
         for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32)
-            keys[v * S + u] = Traits<DT>::key(load_px<DT>(in, P, gx0 + u, gy0 + v));
+            keys[v * S + u] = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
     }
     __syncthreads();
     const int area = S * P.SH;
@@ -539,7 +549,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     for (int v = tid; v < P.N; v += nthreads) {
         const int pos = (int)bufB[v];
         const int y = (int)__umulhi((unsigned)pos, P.div_magic);
-        om[v] = Loc<W>::pack(pos - y * S, y, P);
+        om[v] = Loc<W>::pack(pos - y * S, y, P.cx0, P.cy0);
     }
 }
 
@@ -563,6 +573,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     const int ty0 = (tile / P.tiles_x) * TY;
     const int gx0 = tx0 + P.xmin;  // global coordinates of bounding-box pixel (0, 0)
     const int gy0 = ty0 + P.ymin;
+    const int cx0 = P.cx0, cy0 = P.cy0, xmin = P.xmin, ymin = P.ymin, hist_shift = P.hist_shift;
 
     const int2* vtab = reinterpret_cast<const int2*>(smem + P.off_vtab);
     const int2* htab = reinterpret_cast<const int2*>(smem + P.off_htab);
@@ -590,7 +601,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     stamp(P, tile, 2);
     for (int v = tid; v < N; v += nthreads) {
         const uint32_t e = om[v];
-        ord[(Loc<W>::y(e) + P.cy0) * SP + Loc<W>::x(e) + P.cx0] = (uint16_t)v;
+        ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)v;
     }
     __syncthreads();
 
@@ -611,7 +622,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     for (int sd = warp; sd < P.RB * P.G; sd += nwarps) {
         const int band = sd / P.G, g = sd % P.G;
         const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
-        const int cu = s - P.xmin, cv = t - P.ymin;             // window centre in the box
+        const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
         // one histogram per concurrently solved seed
         uint32_t* hw = shist + (nwarps >= P.RB * P.G ? sd : warp) * kSeedBins;
         for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
@@ -621,10 +632,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         for (int i = lane; i < P.nrows; i += 32) {
             const int sp = spans[i];
             const int width = span_hi(sp) - span_lo(sp) + 1;
-            const uint16_t* row = ord + (cv + P.ymin + i) * SP + cu + span_lo(sp);
+            const uint16_t* row = ord + (cv + ymin + i) * SP + cu + span_lo(sp);
             int x = (lane * 37) % width;
             for (int k = 0; k < width; ++k) {
-                atomicAdd(&hw[row[x] >> P.hist_shift], 1u);
+                atomicAdd(&hw[row[x] >> hist_shift], 1u);
                 x = (x + 1 == width) ? 0 : x + 1;
             }
         }
@@ -654,7 +665,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         const int src_lane = __ffs(who) - 1;
         bin = __shfl_sync(kFull, bin, src_lane);
         below = __shfl_sync(kFull, below, src_lane);
-        const int m = ballot_select(om, N, bin << P.hist_shift, below, target, cu - P.cx0, cv - P.cy0, member);
+        const int m = ballot_select(om, N, bin << hist_shift, below, target, cu - cx0, cv - cy0, member);
         if (m < 0) set_status(FIM_ERR_INTERNAL);
         if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
         __syncwarp();
@@ -669,8 +680,8 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         int s = g * GW + GW / 2;
         const int t = band * BH + BH / 2;
         const int steps = right ? (GW - GW / 2 - 1) : (GW / 2);
-        int cu = s - P.xmin;
-        const int cv = t - P.ymin;
+        int cu = s - xmin;
+        const int cv = t - ymin;
         int p = med[t * TX + s];
         for (int k = 0; k < steps; ++k) {
             const uint16_t* ctr = ord + cv * SP + cu;
@@ -684,7 +695,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             d = __reduce_add_sync(kFull, d);
             cu += right ? 1 : -1;
             s += right ? 1 : -1;
-            const int m = ballot_select(om, N, p, target + d, target, cu - P.cx0, cv - P.cy0, member);
+            const int m = ballot_select(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
             if (m < 0) set_status(FIM_ERR_INTERNAL);
             p = max(m, 0);
             if (lane == 0) med[t * TX + s] = (uint16_t)p;
@@ -703,8 +714,8 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         const int s = cg * 32 + lane;
         int t = band * BH + BH / 2;
         const int steps = down ? (BH - BH / 2 - 1) : (BH / 2);
-        const int cu = s - P.xmin;
-        int cv = t - P.ymin;
+        const int cu = s - xmin;
+        int cv = t - ymin;
         int p = med[t * TX + s];
         const int ncols = P.ncols;
         const int eoff = down ? 0 : -SP;
@@ -726,7 +737,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             }
             cv += down ? 1 : -1;
             t += down ? 1 : -1;
-            const int mine = thread_select<SHAPE, W>(om, N, p, target + d, target, cu - P.cx0, cv - P.cy0, member);
+            const int mine = thread_select<SHAPE, W>(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
             if (mine < 0) set_status(FIM_ERR_INTERNAL);
             p = max(mine, 0);
             med[t * TX + s] = (uint16_t)p;
@@ -736,15 +747,16 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
 
     // ---- 6. output: the input value at Omega[m] ------------------------------------------------
     stamp(P, tile, 6);
-    const char* in = static_cast<const char*>(P.in);
+    const Img im(P);
     char* out = static_cast<char*>(P.out);
+    const int txshift = P.txshift;
     for (int idx = tid; idx < TX * TY; idx += nthreads) {
-        const int t = idx >> P.txshift, s = idx & (TX - 1);
+        const int t = idx >> txshift, s = idx & (TX - 1);
         const int gx = tx0 + s, gy = ty0 + t;
-        if (gx >= P.w || gy >= P.h) continue;
+        if (gx >= im.w || gy >= im.h) continue;
         const uint32_t e = om[med[idx]];
-        const V val = load_px<DT>(in, P, gx0 + Loc<W>::x(e) + P.cx0, gy0 + Loc<W>::y(e) + P.cy0);
-        reinterpret_cast<V*>(out + (long long)gy * P.pitch)[gx] = val;
+        const V val = load_px<DT>(im, gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
+        reinterpret_cast<V*>(out + (long long)gy * im.pitch)[gx] = val;
     }
     __syncthreads();
     stamp(P, tile, 7);
@@ -817,6 +829,9 @@ __device__ void dispatch_tile(const Plan* P, int tile, unsigned char* gslice) {
 
 __global__ void __launch_bounds__(1024, 1) batch_median_kernel(const __grid_constant__ BatchArgs A) {
     __shared__ int s_tile, s_job;
+    // the current job's plan scalars (everything before the tables), so that the tile pipeline
+    // reads them from shared memory rather than global memory
+    __shared__ __align__(16) unsigned char s_plan[kPlanScalarBytes];
     const int tid = threadIdx.x;
     unsigned char* gslice = A.scratch + 256 + (size_t)blockIdx.x * (size_t)A.scratch_per_cta;
     unsigned int* counter = reinterpret_cast<unsigned int*>(A.scratch);
@@ -840,13 +855,17 @@ __global__ void __launch_bounds__(1024, 1) batch_median_kernel(const __grid_cons
         const int job = s_job;
         const int t = s_tile;
         if (job < 0) break;
-        const Plan* P = A.plans + job;
         if (job != cur) {
-            load_tables(*P);
+            const Plan* G = A.plans + job;
+            load_tables(*G);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(G);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(s_plan);
+            for (int i = tid; i < (int)(kPlanScalarBytes / 4); i += blockDim.x) dst[i] = src[i];
             __syncthreads();
             cur = job;
         }
-        dispatch_tile(P, t - A.prefix[job], gslice);  // every plan of a batch has this CTA size
+        // every plan of a batch has this CTA size; the pipeline reads only the plan's scalars
+        dispatch_tile(reinterpret_cast<const Plan*>(s_plan), t - A.prefix[job], gslice);
         __syncthreads();
     }
 }
