@@ -15,7 +15,7 @@ using namespace fim;
 
 struct fim_batch {
     int njobs = 0;
-    int total_tiles = 0;
+    int total_tiles = 0, total_items = 0, max_groups = 1;
     int grid = 0, threads = 0, smem = 0;
     long long scratch_per_cta = 0;
     Plan* d_plans = nullptr;
@@ -53,8 +53,8 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
     *out = nullptr;
     const int limit = device_smem_limit();
     if (limit <= 0) return FIM_ERR_CUDA;
-    std::vector<TileShape> shapes((size_t)count);
-    int cta = 32;
+    constexpr int kCta = 1024;  // every batch CTA; jobs with smaller configurations run several groups
+    std::vector<Plan> plans((size_t)count);
     for (int i = 0; i < count; ++i) {
         const fim_job& j = jobs[i];
         if (!j.in || !j.out || !j.kernel || j.w <= 0 || j.h <= 0) return FIM_ERR_INVALID_ARG;
@@ -62,52 +62,62 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
         const size_t es = (size_t)esize(j.dtype);
         if (j.pitch_bytes < (size_t)j.w * es || j.pitch_bytes % es != 0) return FIM_ERR_INVALID_ARG;
         if (!(j.percentile < 0.0 || j.percentile <= 100.0)) return FIM_ERR_INVALID_ARG;
-        fim_status s = choose_tile(j.kernel, j.dtype, limit, &shapes[i], 1024);
+        TileShape ts;
+        fim_status s = choose_tile(j.kernel, j.dtype, limit, &ts);
         if (s != FIM_OK) return s;
-        cta = std::max(cta, 2 * shapes[i].Tx * shapes[i].RB);
-    }
-    std::vector<Plan> plans((size_t)count);
-    for (int i = 0; i < count; ++i) {
-        const fim_job& j = jobs[i];
         const int n = j.kernel->n;
         int rank = (n - 1) / 2;
         if (j.percentile >= 0.0) rank = std::min(std::max((int)(j.percentile / 100.0 * (n - 1) + 0.5), 0), n - 1);
-        fim_status s = make_plan(j.kernel, j.dtype, rank, j.w, j.h, shapes[i], limit, &plans[i], cta);
+        Plan& p = plans[i];
+        s = make_plan(j.kernel, j.dtype, rank, j.w, j.h, ts, limit, &p);
         if (s != FIM_OK) return s;
-        plans[i].in = j.in;
-        plans[i].out = j.out;
-        plans[i].pitch = (long long)j.pitch_bytes;
-        plans[i].ntiles = plans[i].tiles_x * plans[i].tiles_y;
+        p.in = j.in;
+        p.out = j.out;
+        p.pitch = (long long)j.pitch_bytes;
+        p.ntiles = p.tiles_x * p.tiles_y;
+        // as many groups as fit the CTA and shared memory, but no more than the job has tiles
+        int groups = kCta / p.threads;
+        while (groups > 1 && p.tab_bytes + (size_t)groups * p.group_bytes > (size_t)limit) --groups;
+        p.groups = std::max(1, std::min(groups, p.ntiles));
     }
     std::vector<int> order((size_t)count);
     std::iota(order.begin(), order.end(), 0);
+    // an item's groups run side by side, so an item lasts about one tile of its job
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return tile_cost(plans[a]) > tile_cost(plans[b]); });
     std::vector<Plan> sorted((size_t)count);
     std::vector<int> prefix((size_t)count + 1, 0);
-    long long total = 0;
-    long long spc = 0;
+    long long items = 0, tiles = 0, spc = 0;
+    int smem = 0, max_groups = 1;
     for (int i = 0; i < count; ++i) {
-        sorted[i] = plans[order[i]];
-        prefix[i] = (int)total;
-        total += sorted[i].ntiles;
-        spc = std::max(spc, sorted[i].scratch_per_cta);
+        Plan& p = sorted[i];
+        p = plans[order[i]];
+        prefix[i] = (int)items;
+        items += (p.ntiles + p.groups - 1) / p.groups;
+        tiles += p.ntiles;
+        spc = std::max(spc, p.scratch_per_cta);
+        smem = std::max(smem, p.tab_bytes + p.groups * p.group_bytes);
+        max_groups = std::max(max_groups, p.groups);
     }
-    if (total > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
-    prefix[count] = (int)total;
+    if (items > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
+    prefix[count] = (int)items;
     fim_batch* b = new (std::nothrow) fim_batch();
     if (!b) return FIM_ERR_OOM;
     cudaGetDevice(&b->device);
     b->njobs = count;
-    b->total_tiles = (int)total;
+    b->total_tiles = (int)tiles;
+    b->total_items = (int)items;
+    b->max_groups = max_groups;
     b->scratch_per_cta = spc;
-    fim_status s = batch_prepare(sorted.data(), count, &b->smem, &b->threads);
-    if (s == FIM_OK) s = batch_grid(b->threads, b->smem, total, &b->grid);
+    b->threads = kCta;
+    b->smem = smem;
+    fim_status s = batch_prepare(smem);
+    if (s == FIM_OK) s = batch_grid(b->threads, b->smem, items, &b->grid);
     if (s != FIM_OK) {
         free_batch(b);
         return s;
     }
-    const size_t scratch_bytes = 256 + (size_t)b->grid * (size_t)spc;
+    const size_t scratch_bytes = 256 + (size_t)b->grid * (size_t)max_groups * (size_t)spc;
     if (cudaMalloc(&b->d_plans, sizeof(Plan) * (size_t)count) != cudaSuccess ||
         cudaMalloc(&b->d_prefix, sizeof(int) * ((size_t)count + 1)) != cudaSuccess ||
         cudaMalloc(&b->scratch, scratch_bytes) != cudaSuccess) {
@@ -129,9 +139,10 @@ fim_status fim_batch_run(fim_batch* b, void* stream) {
     if (!b) return FIM_ERR_INVALID_ARG;
     BatchArgs a;
     a.plans = b->d_plans;
-    a.prefix = b->d_prefix;
+    a.item_prefix = b->d_prefix;
     a.njobs = b->njobs;
-    a.total_tiles = b->total_tiles;
+    a.total_items = b->total_items;
+    a.max_groups = b->max_groups;
     a.scratch = b->scratch;
     a.scratch_per_cta = b->scratch_per_cta;
     return batch_launch(a, b->grid, b->threads, b->smem, (cudaStream_t)stream);

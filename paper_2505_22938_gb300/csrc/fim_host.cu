@@ -265,6 +265,9 @@ fim_status layout_plan(Plan* p, int smem_limit) {
     take_tab(&p->off_htab, (size_t)p->nrows * 8);
     take_tab(&p->off_spans, (size_t)p->nrows * 4);
     take_tab(&p->off_frow, (size_t)p->SH * 4);
+    p->tab_bytes = (int)tab;  // everything from here on belongs to one tile group
+    p->off_misc = (int)tab;
+    tab += 256;
     auto gloc = [](size_t off) { return -(int)off - 1; };
     p->loc_bins = p->loc_keys = p->loc_a = p->loc_b = p->loc_hist = 0;
     size_t glob = 0;
@@ -334,6 +337,8 @@ fim_status layout_plan(Plan* p, int smem_limit) {
     }
     if (smem > (size_t)smem_limit) return FIM_ERR_UNSUPPORTED;
     p->smem_bytes = (int)align16(smem);
+    p->group_bytes = p->smem_bytes - p->tab_bytes;
+    p->groups = 1;
     p->scratch_per_cta = (long long)glob;
     return FIM_OK;
 }

@@ -68,6 +68,10 @@ struct Plan {
     // Array placement. A location >= 0 is a byte offset into dynamic shared memory; a location
     // < 0 is -(offset + 1) into the CTA's slice of global scratch.
     int off_vtab, off_htab, off_spans, off_frow;   // tables (shared memory, whole kernel)
+    int tab_bytes;                                  // the tables' extent; a tile group's partition follows
+    int off_misc;                                   // 64 words of scan scratch (per group)
+    int group_bytes;                                // bytes of one group's partition (smem_bytes - tab_bytes)
+    int groups;                                     // batches: tile groups of this job run per CTA
     int loc_om;                                     // omnigram (from the end of the sort on)
     int loc_bins;                                   // counting sorts: bins
     int loc_keys, loc_a, loc_b, loc_hist;           // radix sort: keys, ping-pong lists, histograms
@@ -92,10 +96,11 @@ static_assert(offsetof(Plan, frow) % 4 == 0, "plan scalars are copied as 32-bit 
 // Arguments of the batched persistent launch (plans live in device memory).
 struct BatchArgs {
     const Plan* plans;          // njobs plans, device memory
-    const int* prefix;          // njobs + 1 tile prefix sums, device memory
+    const int* item_prefix;     // njobs + 1 prefix sums of queue items (groups tiles each)
     int njobs;
-    int total_tiles;
-    unsigned char* scratch;     // header (256 B: tile counter) + grid * scratch_per_cta
+    int total_items;
+    int max_groups;             // group slots per CTA in the scratch layout
+    unsigned char* scratch;     // header (256 B: queue counter) + grid * max_groups * scratch_per_cta
     long long scratch_per_cta;
 };
 
@@ -135,8 +140,8 @@ void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 // Device launch (fim_tile.cu).
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_device_status(cudaStream_t stream);
-fim_status batch_prepare(Plan* plans, int n, int* smem_max, int* threads_max);
-fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);
+fim_status batch_prepare(int smem);
+fim_status batch_grid(int threads, int smem, long long total_items, int* grid);
 fim_status batch_launch(const BatchArgs& a, int grid, int threads, int smem, cudaStream_t stream);
 
 }  // namespace fim

@@ -106,9 +106,25 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, c
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+// A tile group: the threads that run one tile's pipeline. A CTA holds one group (single-image
+// launches) or several equal groups (batches of small configurations), each with its own
+// named barrier and its own partition of shared memory (everything after the kernel tables).
+struct Grp {
+    int tid, lane, warp;  // group-local indices
+    int nthreads;         // group size (the plan's CTA size)
+    int bar;              // named barrier; 0 is the whole CTA
+    int shift;            // byte shift of this group's shared-memory partition
+    __device__ __forceinline__ void sync() const {
+        if (bar == 0)
+            __syncthreads();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+    }
+};
+
 // Diagnostics: thread 0 records clock64() at phase boundaries when a buffer is attached.
-__device__ __forceinline__ void stamp(const Plan& P, int tile, int phase) {
-    if (P.phase_clock != nullptr && threadIdx.x == 0 && tile < P.phase_tiles)
+__device__ __forceinline__ void stamp(const Plan& P, int tile, int phase, const Grp& G) {
+    if (P.phase_clock != nullptr && G.tid == 0 && tile < P.phase_tiles)
         P.phase_clock[tile * 8 + phase] = clock64();
 }
 
@@ -296,9 +312,8 @@ __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restric
 
 // Block-wide exclusive scan of 65536 16-bit counters packed two per word (bin 2k in the low
 // half of word k). Offsets stay below 2^16 because the footprint holds at most 65535 pixels.
-__device__ void scan_bins16(uint32_t* bins, const Plan& P) {
-    __shared__ uint32_t wtot[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ void scan_bins16(uint32_t* bins, uint32_t* wtot, const Plan& P, const Grp& G) {
+    const int lane = G.lane, warp = G.warp;
     const int chunk = 32768 / P.nwarps;  // words per warp, a multiple of 128
     uint4* b4 = reinterpret_cast<uint4*>(bins + warp * chunk);
     uint32_t acc = 0;
@@ -309,7 +324,7 @@ __device__ void scan_bins16(uint32_t* bins, const Plan& P) {
     }
     acc = __reduce_add_sync(kFull, acc);
     if (lane == 0) wtot[warp] = acc;
-    __syncthreads();
+    G.sync();
     if (warp == 0) {
         const uint32_t x = lane < P.nwarps ? wtot[lane] : 0;
         uint32_t incl = x;
@@ -319,7 +334,7 @@ __device__ void scan_bins16(uint32_t* bins, const Plan& P) {
         }
         wtot[lane] = incl - x;
     }
-    __syncthreads();
+    G.sync();
     uint32_t run = wtot[warp];
     for (int it = 0; it < chunk / 128; ++it) {
         uint4 q = b4[it * 32 + lane];
@@ -341,7 +356,7 @@ __device__ void scan_bins16(uint32_t* bins, const Plan& P) {
         b4[it * 32 + lane] = make_uint4(w[0], w[1], w[2], w[3]);
         run += __shfl_sync(kFull, incl, 31);
     }
-    __syncthreads();
+    G.sync();
 }
 
 // The image as the tile pipeline reads it, held in registers.
@@ -364,16 +379,16 @@ __device__ __forceinline__ typename Traits<DT>::T load_px(const Img& im, int gx,
 // footprint, exclusive prefix, then every pixel takes the next free ordinal of its value.
 // Ties get consecutive ordinals in arrival order, which is all the method needs.
 template <int DT, int W>
-__device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t* bins, typename Loc<W>::E* om,
-                                        int gx0, int gy0) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t* bins, uint32_t* misc,
+                                        typename Loc<W>::E* om, int gx0, int gy0, const Grp& G) {
+    const int tid = G.tid, lane = G.lane, warp = G.warp;
     const Img im(P);
     const int SH = P.SH, nwarps = P.nwarps, cx0 = P.cx0, cy0 = P.cy0;
     constexpr bool k16 = DT == FIM_U16;
     const int nwords = k16 ? 32768 : 256;
     for (int i = tid * 4; i < nwords; i += P.threads * 4)
         *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
-    __syncthreads();
+    G.sync();
     for (int v = warp; v < SH; v += nwarps) {
         const int fr = frow[v];
         for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
@@ -384,9 +399,9 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
                 atomicAdd(&bins[key], 1u);
         }
     }
-    __syncthreads();
+    G.sync();
     if (k16) {
-        scan_bins16(bins, P);
+        scan_bins16(bins, misc, P, G);
     } else {
         if (warp == 0) {
             uint32_t c[8], s = 0;
@@ -407,7 +422,7 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
                 b += c[k];
             }
         }
-        __syncthreads();
+        G.sync();
     }
     for (int v = warp; v < SH; v += nwarps) {
         const int fr = frow[v];
@@ -433,10 +448,10 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
 // list B, which is then rewritten in place as the omnigram.
 template <int DT, int W>
 __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t* keys, typename Loc<W>::Pos* bufA,
-                                        typename Loc<W>::Pos* bufB, uint32_t* hist, int gx0, int gy0) {
+                                        typename Loc<W>::Pos* bufB, uint32_t* hist, uint32_t* wsum, int gx0, int gy0,
+                                        const Grp& G) {
     using Pos = typename Loc<W>::Pos;
-    __shared__ uint32_t wsum[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = G.tid, lane = G.lane, warp = G.warp;
     const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
     constexpr int HS = kSortBins + 1;
     const Img im(P);
@@ -445,7 +460,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
         for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32)
             keys[v * S + u] = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
     }
-    __syncthreads();
+    G.sync();
     const int area = S * P.SH;
     const Pos* src = nullptr;
     Pos* dst = bufA;
@@ -477,7 +492,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
             if (valid && lane == __ffs(peers) - 1) hw[d] += __popc(peers);
             __syncwarp();
         }
-        __syncthreads();
+        G.sync();
         {   // exclusive scan in (digit, warp) order: each thread takes 8 consecutive counters
             const int e0 = tid * 8;  // 256 * nwarps counters over 32 * nwarps threads
             uint32_t c[8];
@@ -494,7 +509,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
                 if (lane >= o) incl += t;
             }
             if (lane == 31) wsum[warp] = incl;
-            __syncthreads();
+            G.sync();
             if (warp == 0) {
                 const uint32_t x = lane < nwarps ? wsum[lane] : 0;
                 uint32_t y = x;
@@ -504,7 +519,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
                 }
                 wsum[lane] = y - x;
             }
-            __syncthreads();
+            G.sync();
             uint32_t run = incl - local + wsum[warp];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -513,7 +528,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
                 run += c[j];
             }
         }
-        __syncthreads();
+        G.sync();
         for (int b = s0; b < s1; b += 32) {
             const int i = b + lane;
             bool valid = i < s1;
@@ -540,7 +555,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
             }
             __syncwarp();
         }
-        __syncthreads();
+        G.sync();
         src = dst;
         dst = (dst == bufA) ? bufB : bufA;
     }
@@ -559,13 +574,14 @@ __device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, 
 }
 
 template <int DT, int SHAPE, int W, int OG>
-__device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G) {
+    extern __shared__ __align__(16) unsigned char smem_base[];
+    unsigned char* const smem = smem_base + G.shift;  // this group's partition (tables excluded)
     using V = typename Traits<DT>::T;
     using E = typename Loc<W>::E;
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
+    const int tid = G.tid;
+    const int lane = G.lane;
+    const int warp = G.warp;
     const int nthreads = P.threads;
     const int nwarps = P.nwarps;
     const int SP = P.SP, N = P.N, TX = P.Tx, TY = P.Ty;
@@ -575,10 +591,11 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     const int gy0 = ty0 + P.ymin;
     const int cx0 = P.cx0, cy0 = P.cy0, xmin = P.xmin, ymin = P.ymin, hist_shift = P.hist_shift;
 
-    const int2* vtab = reinterpret_cast<const int2*>(smem + P.off_vtab);
-    const int2* htab = reinterpret_cast<const int2*>(smem + P.off_htab);
-    const int* spans = reinterpret_cast<const int*>(smem + P.off_spans);
-    const int* frow = reinterpret_cast<const int*>(smem + P.off_frow);
+    const int2* vtab = reinterpret_cast<const int2*>(smem_base + P.off_vtab);
+    const int2* htab = reinterpret_cast<const int2*>(smem_base + P.off_htab);
+    const int* spans = reinterpret_cast<const int*>(smem_base + P.off_spans);
+    const int* frow = reinterpret_cast<const int*>(smem_base + P.off_frow);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(smem + P.off_misc);
     // The omnigram's home is fixed per instantiation (OG), so the compiler keeps shared-memory
     // accesses as such; everything else of the solve always lives in shared memory.
     E* om = OG ? reinterpret_cast<E*>(gslice + (-(long long)P.loc_om - 1)) : reinterpret_cast<E*>(smem + P.loc_om);
@@ -587,23 +604,24 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + P.loc_shist);
 
     // ---- 1. ordinal transform ------------------------------------------------------------------
-    stamp(P, tile, 1);
+    stamp(P, tile, 1, G);
     if constexpr (DT == FIM_F32)
         ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
                                        place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
                                        place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
-                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), gx0, gy0);
+                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, gx0, gy0, G);
     else
-        ordinal_transform_count<DT, W>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), om, gx0, gy0);
-    __syncthreads();
+        ordinal_transform_count<DT, W>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), misc, om, gx0, gy0,
+                                       G);
+    G.sync();
 
     // ---- 2. ordinal image I (Eq. 4) ------------------------------------------------------------
-    stamp(P, tile, 2);
+    stamp(P, tile, 2, G);
     for (int v = tid; v < N; v += nthreads) {
         const uint32_t e = om[v];
         ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)v;
     }
-    __syncthreads();
+    G.sync();
 
     Member<SHAPE, W> member;
     if constexpr (SHAPE == kShapeDisk) {
@@ -618,7 +636,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     const int GW = TX / P.G;       // seed spacing within a seed row
 
     // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
-    stamp(P, tile, 3);
+    stamp(P, tile, 3, G);
     for (int sd = warp; sd < P.RB * P.G; sd += nwarps) {
         const int band = sd / P.G, g = sd % P.G;
         const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
@@ -670,10 +688,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
         __syncwarp();
     }
-    __syncthreads();
+    G.sync();
 
     // ---- 4. seed rows: horizontal slides, lanes split the kernel rows ----------------------
-    stamp(P, tile, 4);
+    stamp(P, tile, 4, G);
     for (int job = warp; job < 2 * P.RB * P.G; job += nwarps) {
         const int sd = job >> 1, right = job & 1;
         const int band = sd / P.G, g = sd % P.G;
@@ -701,10 +719,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             if (lane == 0) med[t * TX + s] = (uint16_t)p;
         }
     }
-    __syncthreads();
+    G.sync();
 
     // ---- 5. vertical sweeps: thread per window column, per-thread refinement ----------------
-    stamp(P, tile, 5);
+    stamp(P, tile, 5, G);
     if (warp < P.vthreads / 32) {
         const int groups = TX / 32;
         const int cg = warp % groups;
@@ -743,10 +761,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             med[t * TX + s] = (uint16_t)p;
         }
     }
-    __syncthreads();
+    G.sync();
 
     // ---- 6. output: the input value at Omega[m] ------------------------------------------------
-    stamp(P, tile, 6);
+    stamp(P, tile, 6, G);
     const Img im(P);
     char* out = static_cast<char*>(P.out);
     const int txshift = P.txshift;
@@ -758,8 +776,8 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         const V val = load_px<DT>(im, gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
         reinterpret_cast<V*>(out + (long long)gy * im.pitch)[gx] = val;
     }
-    __syncthreads();
-    stamp(P, tile, 7);
+    G.sync();
+    stamp(P, tile, 7, G);
 }
 
 __device__ __forceinline__ void load_tables(const Plan& P) {
@@ -786,13 +804,14 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
     unsigned char* gslice = P.scratch + 256 + (size_t)blockIdx.x * (size_t)P.scratch_per_cta;
     load_tables(P);
     unsigned int* counter = reinterpret_cast<unsigned int*>(P.scratch);
+    const Grp G{tid, tid & 31, tid >> 5, (int)blockDim.x, 0, 0};
     for (;;) {
         if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
         __syncthreads();
         const int tile = s_tile;
         if (tile >= P.ntiles) break;
-        stamp(P, tile, 0);
-        process_tile<DT, SHAPE, W, OG>(P, tile, gslice);
+        stamp(P, tile, 0, G);
+        process_tile<DT, SHAPE, W, OG>(P, tile, gslice, G);
     }
 }
 
@@ -802,22 +821,22 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
 // prefix table, loads the job's tables into shared memory when its job changes, and runs the
 // job's instantiation of the tile pipeline.
 template <int DT, int SHAPE, int W, int OG>
-__device__ __noinline__ void batch_tile(const Plan* P, int tile, unsigned char* gslice) {
-    process_tile<DT, SHAPE, W, OG>(*P, tile, gslice);
+__device__ __noinline__ void batch_tile(const Plan* P, int tile, unsigned char* gslice, const Grp& G) {
+    process_tile<DT, SHAPE, W, OG>(*P, tile, gslice, G);
 }
 
-__device__ void dispatch_tile(const Plan* P, int tile, unsigned char* gslice) {
+__device__ void dispatch_tile(const Plan* P, int tile, unsigned char* gslice, const Grp& G) {
     const int cls = P->wide ? 2 : (P->loc_om < 0 ? 1 : 0);
     const bool disk = P->shape == kShapeDisk;
 #define FIM_CASE(DT)                                                                   \
     if (disk) {                                                                        \
-        if (cls == 0) batch_tile<DT, kShapeDisk, 0, 0>(P, tile, gslice);              \
-        else if (cls == 1) batch_tile<DT, kShapeDisk, 0, 1>(P, tile, gslice);         \
-        else batch_tile<DT, kShapeDisk, 1, 1>(P, tile, gslice);                       \
+        if (cls == 0) batch_tile<DT, kShapeDisk, 0, 0>(P, tile, gslice, G);           \
+        else if (cls == 1) batch_tile<DT, kShapeDisk, 0, 1>(P, tile, gslice, G);      \
+        else batch_tile<DT, kShapeDisk, 1, 1>(P, tile, gslice, G);                    \
     } else {                                                                           \
-        if (cls == 0) batch_tile<DT, kShapeSpans, 0, 0>(P, tile, gslice);             \
-        else if (cls == 1) batch_tile<DT, kShapeSpans, 0, 1>(P, tile, gslice);        \
-        else batch_tile<DT, kShapeSpans, 1, 1>(P, tile, gslice);                      \
+        if (cls == 0) batch_tile<DT, kShapeSpans, 0, 0>(P, tile, gslice, G);          \
+        else if (cls == 1) batch_tile<DT, kShapeSpans, 0, 1>(P, tile, gslice, G);     \
+        else batch_tile<DT, kShapeSpans, 1, 1>(P, tile, gslice, G);                   \
     }
     switch (P->dtype) {
         case FIM_U8: FIM_CASE(FIM_U8) break;
@@ -828,44 +847,55 @@ __device__ void dispatch_tile(const Plan* P, int tile, unsigned char* gslice) {
 }
 
 __global__ void __launch_bounds__(1024, 1) batch_median_kernel(const __grid_constant__ BatchArgs A) {
-    __shared__ int s_tile, s_job;
+    __shared__ int s_job, s_first, s_count;
     // the current job's plan scalars (everything before the tables), so that the tile pipeline
     // reads them from shared memory rather than global memory
     __shared__ __align__(16) unsigned char s_plan[kPlanScalarBytes];
     const int tid = threadIdx.x;
-    unsigned char* gslice = A.scratch + 256 + (size_t)blockIdx.x * (size_t)A.scratch_per_cta;
     unsigned int* counter = reinterpret_cast<unsigned int*>(A.scratch);
     int cur = -1;
     for (;;) {
         if (tid == 0) {
-            const int t = (int)atomicAdd(counter, 1u);
-            int j = -1;
-            if (t < A.total_tiles) {  // binary search: prefix[j] <= t < prefix[j + 1]
+            // one queue item = up to `groups` consecutive tiles of one job, run side by side
+            const int item = (int)atomicAdd(counter, 1u);
+            int j = -1, first = 0, count = 0;
+            if (item < A.total_items) {  // binary search: item_prefix[j] <= item < item_prefix[j + 1]
                 int lo = 0, hi = A.njobs - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (A.prefix[mid] <= t) lo = mid; else hi = mid - 1;
+                    if (A.item_prefix[mid] <= item) lo = mid; else hi = mid - 1;
                 }
                 j = lo;
+                const Plan* Pj = A.plans + j;
+                first = (item - A.item_prefix[j]) * Pj->groups;
+                count = min(Pj->groups, Pj->ntiles - first);
             }
-            s_tile = t;
             s_job = j;
+            s_first = first;
+            s_count = count;
         }
         __syncthreads();
         const int job = s_job;
-        const int t = s_tile;
         if (job < 0) break;
         if (job != cur) {
-            const Plan* G = A.plans + job;
-            load_tables(*G);
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(G);
+            const Plan* Gp = A.plans + job;
+            load_tables(*Gp);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(Gp);
             uint32_t* dst = reinterpret_cast<uint32_t*>(s_plan);
             for (int i = tid; i < (int)(kPlanScalarBytes / 4); i += blockDim.x) dst[i] = src[i];
             __syncthreads();
             cur = job;
         }
-        // every plan of a batch has this CTA size; the pipeline reads only the plan's scalars
-        dispatch_tile(reinterpret_cast<const Plan*>(s_plan), t - A.prefix[job], gslice);
+        const Plan* P = reinterpret_cast<const Plan*>(s_plan);
+        const int T = P->threads;
+        const int g = tid / T;
+        if (g < s_count) {
+            const int lt = tid - g * T;
+            const Grp G{lt, lt & 31, lt >> 5, T, T == (int)blockDim.x ? 0 : 1 + g, g * P->group_bytes};
+            unsigned char* gslice =
+                A.scratch + 256 + ((size_t)blockIdx.x * A.max_groups + g) * (size_t)A.scratch_per_cta;
+            dispatch_tile(P, s_first + g, gslice, G);
+        }
         __syncthreads();
     }
 }
@@ -914,29 +944,22 @@ fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
     return FIM_ERR_INVALID_ARG;
 }
 
-fim_status batch_prepare(Plan* plans, int n, int* smem_max, int* threads_max) {
-    int smem = 0, thr = 32;
-    for (int i = 0; i < n; ++i) {
-        smem = std::max(smem, plans[i].smem_bytes);
-        thr = std::max(thr, plans[i].threads);
-    }
+fim_status batch_prepare(int smem) {
     if (cudaFuncSetAttribute(batch_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
         cudaGetLastError();
         return FIM_ERR_CUDA;
     }
-    *smem_max = smem;
-    *threads_max = thr;
     return FIM_OK;
 }
 
-fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid) {
+fim_status batch_grid(int threads, int smem, long long total_items, int* grid) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_median_kernel, threads, smem) != cudaSuccess ||
         occ < 1) {
         cudaGetLastError();
         return FIM_ERR_UNSUPPORTED;
     }
-    *grid = (int)std::min<long long>(total_tiles, (long long)occ * device_sm_count());
+    *grid = (int)std::min<long long>(total_items, (long long)occ * device_sm_count());
     return FIM_OK;
 }
 
