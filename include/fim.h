@@ -102,6 +102,24 @@ fim_status fim_median(const void* in, void* out, int w, int h, size_t pitch_byte
                       const fim_kernel* k, fim_border border, void* stream);
 
 /*
+ * fim_median for callers that must not allocate device memory (no cudaMalloc, cudaFree or any
+ * allocating library call on this path): work inside stream capture, services whose device
+ * memory belongs to an external pool, real-time code that allocates only at start-up. The paper
+ * has no counterpart; it is an API convenience of this library.
+ * Same arguments and result as fim_median. Its workspace is one fixed array of
+ * FIM_NOALLOC_WORKSPACE_BYTES of device memory inside the library, held by every GPU that loads
+ * the library until the process exits. The first call on each device looks up the array's
+ * address (cudaGetSymbolAddress); make that first call before any stream capture. Calls needing
+ * more workspace than the array holds (large kernels on large images: the per-CTA buffers of
+ * kernels whose footprint does not fit in shared memory) return FIM_ERR_UNSUPPORTED and launch
+ * nothing. All calls share the array, so calls whose work overlaps on the GPU (different streams
+ * without ordering) race: serialise them.
+ */
+#define FIM_NOALLOC_WORKSPACE_BYTES (16u << 20)
+fim_status fim_median_noalloc(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                              const fim_kernel* k, fim_border border, void* stream);
+
+/*
  * Percentile (rank-order) filter: the same method with target rank
  * rank = round(percentile / 100 * (n - 1)) instead of (n - 1) / 2 (Sec. 6.2.5, Fig. 12-14).
  * percentile in [0, 100].

@@ -40,6 +40,7 @@ SIGNATURES = {
     "fim_percentile": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_double,
                                   _c.c_int, _P]),
     "fim_median_host": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
+    "fim_median_noalloc": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
     "fim_sync_status": (_c.c_int, [_P]),
     "fim_status_string": (_c.c_char_p, [_c.c_int]),
     "fim_version": (_c.c_char_p, []),
@@ -161,6 +162,13 @@ def fim_median(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtyp
     """Raw C-ABI call on device pointers (asynchronous on `stream`)."""
     _check(lib().fim_median(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, border, stream or None),
            "fim_median")
+
+
+def fim_median_noalloc(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+                       stream: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
+    """fim_median without any device allocation: uses the library's fixed device workspace."""
+    _check(lib().fim_median_noalloc(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, border,
+                                    stream or None), "fim_median_noalloc")
 
 
 def fim_percentile(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,

@@ -140,6 +140,7 @@ void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 // Device launch (fim_tile.cu).
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_device_status(cudaStream_t stream);
+fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
 fim_status batch_prepare(int smem);
 fim_status batch_grid(int threads, int smem, long long total_items, int* grid);
 fim_status batch_launch(const BatchArgs& a, int grid, int threads, int smem, cudaStream_t stream);

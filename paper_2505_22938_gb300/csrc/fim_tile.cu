@@ -926,6 +926,39 @@ fim_status launch_typed(Plan& p, cudaStream_t stream) {
     return FIM_OK;
 }
 
+// Same launch, but on a caller-provided workspace of fixed capacity (no allocation). Returns
+// FIM_ERR_UNSUPPORTED when this launch would need more workspace than `capacity` bytes.
+template <int DT, int SHAPE, int W, int OG>
+fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
+    auto fn = tile_median_kernel<DT, SHAPE, W, OG>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FIM_ERR_CUDA;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p.threads, p.smem_bytes) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return FIM_ERR_UNSUPPORTED;
+    }
+    const long long tiles = (long long)p.tiles_x * p.tiles_y;
+    if (tiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
+    p.ntiles = (int)tiles;
+    const int grid = (int)std::min<long long>(tiles, (long long)occ * device_sm_count());
+    if (256 + (unsigned long long)grid * (unsigned long long)p.scratch_per_cta > capacity) return FIM_ERR_UNSUPPORTED;
+    p.scratch = scratch;
+    if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;  // tile queue counter
+    fn<<<grid, p.threads, p.smem_bytes, stream>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;
+    return FIM_OK;
+}
+
+template <int DT, int SHAPE>
+fim_status launch_w_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
+    if (p.wide) return launch_typed_fixed<DT, SHAPE, 1, 1>(p, scratch, capacity, stream);
+    return p.loc_om < 0 ? launch_typed_fixed<DT, SHAPE, 0, 1>(p, scratch, capacity, stream)
+                        : launch_typed_fixed<DT, SHAPE, 0, 0>(p, scratch, capacity, stream);
+}
+
 template <int DT, int SHAPE>
 fim_status launch_w(Plan& p, cudaStream_t stream) {
     if (p.wide) return launch_typed<DT, SHAPE, 1, 1>(p, stream);
@@ -940,6 +973,22 @@ fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
         case FIM_U8: return disk ? launch_w<FIM_U8, kShapeDisk>(p, stream) : launch_w<FIM_U8, kShapeSpans>(p, stream);
         case FIM_U16: return disk ? launch_w<FIM_U16, kShapeDisk>(p, stream) : launch_w<FIM_U16, kShapeSpans>(p, stream);
         case FIM_F32: return disk ? launch_w<FIM_F32, kShapeDisk>(p, stream) : launch_w<FIM_F32, kShapeSpans>(p, stream);
+    }
+    return FIM_ERR_INVALID_ARG;
+}
+
+fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
+    const bool disk = p.shape == kShapeDisk;
+    switch (p.dtype) {
+        case FIM_U8:
+            return disk ? launch_w_fixed<FIM_U8, kShapeDisk>(p, scratch, capacity, stream)
+                        : launch_w_fixed<FIM_U8, kShapeSpans>(p, scratch, capacity, stream);
+        case FIM_U16:
+            return disk ? launch_w_fixed<FIM_U16, kShapeDisk>(p, scratch, capacity, stream)
+                        : launch_w_fixed<FIM_U16, kShapeSpans>(p, scratch, capacity, stream);
+        case FIM_F32:
+            return disk ? launch_w_fixed<FIM_F32, kShapeDisk>(p, scratch, capacity, stream)
+                        : launch_w_fixed<FIM_F32, kShapeSpans>(p, scratch, capacity, stream);
     }
     return FIM_ERR_INVALID_ARG;
 }
