@@ -191,6 +191,84 @@ void fim_batch_destroy(fim_batch* b);
 fim_status fim_median_batch(const fim_job* jobs, int count, void* stream);
 
 /*
+ * Learned rank bracket for the seed windows (not part of the paper; the paper's seed windows are
+ * solved from a low-precision histogram, Sec. 4.2). A small network predicts, from a seed
+ * window's features, where its median rank lies; the filter counts the window's members below
+ * both ends of the predicted bracket in one pass and scans the omnigram from the nearer end, so
+ * a bad prediction only lengthens the scan: results stay bit-identical to fim_median.
+ *
+ * Network: 41 features (the tile footprint's 32 value quantiles, normalised by their median and
+ * 1/8-7/8 spread, and the ranks / N of the 3x3 pixels around the window centre) -> 64 ReLU ->
+ * 64 ReLU -> 2 outputs (mu: the median rank as a fraction of the tile's feasible median ranks;
+ * s: log of its standard deviation). bf16 weights, fp32 accumulation. Parameters are one flat
+ * fp32 vector of fim_model_param_count() values: W1[41][64], b1[64], W2[64][64], b2[64], W3[64][2],
+ * b3[2] (row-major, input index first). Training rows are 42 floats: 41 features then the label.
+ */
+typedef struct fim_model fim_model;
+
+/* Number of parameters of the network. */
+int fim_model_param_count(void);
+
+/* New model with He-uniform weights drawn from `seed`. */
+fim_status fim_model_create(uint64_t seed, fim_model** out);
+
+/* Frees a model (waits for the device first). NULL is ignored. */
+void fim_model_destroy(fim_model* m);
+
+/* Copies the fp32 master parameters and/or their bf16 rounding (as used by every forward
+ * pass) to host arrays of fim_model_param_count() elements; either pointer may be NULL. */
+fim_status fim_model_get_params(const fim_model* m, float* host_fp32, uint16_t* host_bf16);
+
+/* Replaces the parameters (host fp32 array); the bf16 copy is re-rounded (nearest even). */
+fim_status fim_model_set_params(fim_model* m, const float* host_fp32);
+
+/* Bracket half-width in predicted standard deviations (set by fim_model_calibrate). */
+float fim_model_bracket_z(const fim_model* m);
+
+/* Forward pass: rows of features (device, row_stride floats apart) -> out[2*i] = mu,
+ * out[2*i+1] = s (device). Synchronous. */
+fim_status fim_model_forward(const fim_model* m, const float* x, int rows, int row_stride, float* out, void* stream);
+
+/* Mean Gaussian negative log-likelihood 0.5 (y - mu)^2 / sigma^2 + log sigma (sigma = e^s, s
+ * clamped to [-8, 2]) of the rows and its gradient with respect to the parameters (as used by
+ * the forward pass) into grad_out (device, may be NULL); loss_out (host, may be NULL). */
+fim_status fim_model_loss_grad(fim_model* m, const float* x, int rows, int row_stride, const float* y, int y_stride,
+                               float* grad_out, float* loss_out, void* stream);
+
+/* Trains on training rows (device) with Adam (beta 0.9 / 0.999), minibatches of `batch`
+ * consecutive rows, for `epochs` passes. Synchronous; last_epoch_loss may be NULL. */
+fim_status fim_model_train(fim_model* m, const float* rows_xy, int rows, int epochs, int batch, float lr,
+                           void* stream, float* last_epoch_loss);
+
+/* Sets the bracket half-width z so that |y - mu| <= z sigma holds for `coverage` of the given
+ * rows (held-out training rows, device). */
+fim_status fim_model_calibrate(fim_model* m, const float* rows_xy, int rows, double coverage, void* stream,
+                               float* z_out);
+
+/* Saves / loads parameters, bracket width and optimiser state (resumable training). */
+fim_status fim_model_save(const fim_model* m, const char* path);
+fim_status fim_model_load(const char* path, fim_model** out);
+
+/*
+ * Runs fim_median (in -> out) and appends one training row per seed window: its features and its
+ * exact median rank as a fraction of the tile's feasible median ranks. rows_xy (device) holds
+ * `capacity` rows; *count_dev (device counter, zeroed by the caller) is advanced by every seed,
+ * even past the capacity (rows beyond it are not written).
+ */
+fim_status fim_collect_seed_samples(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                                    const fim_kernel* k, float* rows_xy, int capacity, unsigned int* count_dev,
+                                    void* stream);
+
+/*
+ * fim_median with the learned seed bracket (model may be NULL: the plain seeds). If stats_dev is
+ * not NULL (device, 5 counters the caller zeroes) the launch adds: seed windows, bracket hits,
+ * misses below the bracket, misses above it, and omnigram ranks the seeds' scans walked.
+ */
+fim_status fim_median_learned(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
+                              const fim_kernel* k, const fim_model* m, fim_border border, void* stream,
+                              unsigned long long* stats_dev);
+
+/*
  * Waits for `stream`, then returns and clears the device status word: FIM_OK, or the
  * first device-side error recorded since the last call (FIM_ERR_TIMEOUT, FIM_ERR_INTERNAL).
  */

@@ -54,7 +54,26 @@ SIGNATURES = {
     "fim_batch_info": (_c.c_int, [_P, _P, _P, _P, _P]),
     "fim_batch_destroy": (None, [_P]),
     "fim_median_batch": (_c.c_int, [_P, _c.c_int, _P]),
+    "fim_model_param_count": (_c.c_int, []),
+    "fim_model_create": (_c.c_int, [_c.c_uint64, _PP]),
+    "fim_model_destroy": (None, [_P]),
+    "fim_model_get_params": (_c.c_int, [_P, _P, _P]),
+    "fim_model_set_params": (_c.c_int, [_P, _P]),
+    "fim_model_bracket_z": (_c.c_float, [_P]),
+    "fim_model_forward": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _P, _P]),
+    "fim_model_loss_grad": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _P, _c.c_int, _P, _P, _P]),
+    "fim_model_train": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_float, _P, _P]),
+    "fim_model_calibrate": (_c.c_int, [_P, _P, _c.c_int, _c.c_double, _P, _P]),
+    "fim_model_save": (_c.c_int, [_P, _c.c_char_p]),
+    "fim_model_load": (_c.c_int, [_c.c_char_p, _PP]),
+    "fim_collect_seed_samples": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _P, _c.c_int,
+                                            _P, _P]),
+    "fim_median_learned": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _P, _c.c_int, _P,
+                                      _P]),
 }
+
+N_FEATURES = 41
+ROW = N_FEATURES + 1
 
 
 class fim_job(ctypes.Structure):
@@ -249,6 +268,97 @@ def fim_median_batch(jobs: list, stream: int = 0) -> None:
     arr = (fim_job * len(jobs))(*jobs)
     _check(lib().fim_median_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs), stream or None),
            "fim_median_batch")
+
+
+class Model:
+    """Owns a fim_model handle (the learned seed-bracket network)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @classmethod
+    def create(cls, seed: int = 1) -> "Model":
+        h = ctypes.c_void_p()
+        _check(lib().fim_model_create(int(seed), ctypes.byref(h)), "fim_model_create")
+        return cls(h)
+
+    @classmethod
+    def load(cls, path: str) -> "Model":
+        h = ctypes.c_void_p()
+        _check(lib().fim_model_load(path.encode(), ctypes.byref(h)), "fim_model_load")
+        return cls(h)
+
+    def save(self, path: str) -> None:
+        _check(lib().fim_model_save(self.handle, path.encode()), "fim_model_save")
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib().fim_model_param_count())
+
+    def params(self):
+        import numpy as np
+        n = self.param_count()
+        f = np.empty(n, np.float32)
+        b = np.empty(n, np.uint16)
+        _check(lib().fim_model_get_params(self.handle, f.ctypes.data, b.ctypes.data), "fim_model_get_params")
+        return f, b
+
+    def set_params(self, host_fp32) -> None:
+        import numpy as np
+        a = np.ascontiguousarray(host_fp32, dtype=np.float32)
+        assert a.size == self.param_count()
+        _check(lib().fim_model_set_params(self.handle, a.ctypes.data), "fim_model_set_params")
+
+    @property
+    def bracket_z(self) -> float:
+        return float(lib().fim_model_bracket_z(self.handle))
+
+    def forward(self, x_ptr: int, rows: int, row_stride: int, out_ptr: int, stream: int = 0) -> None:
+        _check(lib().fim_model_forward(self.handle, x_ptr, rows, row_stride, out_ptr, stream or None),
+               "fim_model_forward")
+
+    def loss_grad(self, x_ptr: int, rows: int, row_stride: int, y_ptr: int, y_stride: int, grad_ptr: int,
+                  stream: int = 0) -> float:
+        loss = ctypes.c_float()
+        _check(lib().fim_model_loss_grad(self.handle, x_ptr, rows, row_stride, y_ptr, y_stride, grad_ptr or None,
+                                         ctypes.byref(loss), stream or None), "fim_model_loss_grad")
+        return loss.value
+
+    def train(self, rows_ptr: int, rows: int, epochs: int, batch: int, lr: float, stream: int = 0) -> float:
+        loss = ctypes.c_float()
+        _check(lib().fim_model_train(self.handle, rows_ptr, rows, epochs, batch, float(lr), stream or None,
+                                     ctypes.byref(loss)), "fim_model_train")
+        return loss.value
+
+    def calibrate(self, rows_ptr: int, rows: int, coverage: float, stream: int = 0) -> float:
+        z = ctypes.c_float()
+        _check(lib().fim_model_calibrate(self.handle, rows_ptr, rows, float(coverage), stream or None,
+                                         ctypes.byref(z)), "fim_model_calibrate")
+        return z.value
+
+    def close(self) -> None:
+        if self.handle:
+            lib().fim_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fim_collect_seed_samples(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+                             rows_ptr: int, capacity: int, count_ptr: int, stream: int = 0) -> None:
+    _check(lib().fim_collect_seed_samples(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, rows_ptr,
+                                          capacity, count_ptr, stream or None), "fim_collect_seed_samples")
+
+
+def fim_median_learned(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
+                       model, stream: int = 0, stats_ptr: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
+    _check(lib().fim_median_learned(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle,
+                                    model.handle if model is not None else None, border, stream or None,
+                                    stats_ptr or None), "fim_median_learned")
 
 
 def fim_release_workspace() -> None:

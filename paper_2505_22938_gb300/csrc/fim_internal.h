@@ -20,6 +20,22 @@ constexpr int kSeedBins = 256;    // coarse histogram bins of a seed solve
 
 enum Shape : int { kShapeDisk = 0, kShapeSpans = 1 };
 
+// Rank-bracket MLP: kFeatures inputs -> kHidden -> kHidden -> 2 (predicted rank, log scale).
+constexpr int kQuantiles = 32;   // footprint value quantiles
+constexpr int kNeigh = 9;        // 3x3 neighbourhood ranks of the window centre
+constexpr int kFeatures = kQuantiles + kNeigh;
+constexpr int kHidden = 64;
+constexpr int kMlpParams = kFeatures * kHidden + kHidden + kHidden * kHidden + kHidden + kHidden * 2 + 2;
+// parameter offsets in the flat vector: W1[f][h], b1[h], W2[h][h'], b2[h'], W3[h'][2], b3[2]
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kFeatures * kHidden;
+constexpr int kOffW2 = kOffB1 + kHidden;
+constexpr int kOffB2 = kOffW2 + kHidden * kHidden;
+constexpr int kOffW3 = kOffB2 + kHidden;
+constexpr int kOffB3 = kOffW3 + kHidden * 2;
+// seed statistics: seeds, bracket hits, misses below, misses above, omnigram ranks scanned
+constexpr int kStatSlots = 5;
+
 // Geometry of one tile configuration: output tile Tx x Ty, 2*Tx*RB threads.
 // RB bands of Ty/RB rows; each band's middle row is a seed row with G seeds.
 struct TileShape {
@@ -63,6 +79,13 @@ struct Plan {
     int hist_shift;         // seed histogram: bin = rank >> hist_shift
     int sort;               // SortKind
     int wide;               // 1: footprint box wider than 256: 32-bit omnigram entries and positions
+    // learned rank bracket for the seed windows (all optional; null = the plain histogram seeds)
+    const uint16_t* model;            // bf16 MLP parameters (kMlpParams), device memory
+    float bracket_z;                  // bracket half-width in predicted standard deviations
+    unsigned long long* stats;        // kStatSlots counters, device memory
+    float* samples;                   // training rows: kFeatures features + 1 label each
+    unsigned int* sample_count;       // rows written so far (device counter)
+    int sample_cap;                   // capacity of samples in rows
     unsigned long long* phase_clock;  // optional: 8 clock64() stamps per tile (diagnostics)
     int phase_tiles;                  // capacity of phase_clock in tiles
     // Array placement. A location >= 0 is a byte offset into dynamic shared memory; a location

@@ -568,6 +568,66 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     }
 }
 
+// ---- learned rank bracket (seed windows) ---------------------------------------------------
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// Warp-cooperative forward pass of the bracket MLP (bf16 weights, fp32 accumulation). Lane l
+// holds feature l in fa (l < 32) and feature 32 + l in fb (l < 9). Returns (mu, s) in all lanes.
+__device__ __forceinline__ float2 mlp_forward_warp(const uint16_t* __restrict__ w, float fa, float fb) {
+    const int lane = threadIdx.x & 31;
+    float a0 = bf16_to_f32(__ldg(w + kOffB1 + lane)), a1 = bf16_to_f32(__ldg(w + kOffB1 + lane + 32));
+#pragma unroll 4
+    for (int i = 0; i < kFeatures; ++i) {
+        const float x = i < kQuantiles ? __shfl_sync(kFull, fa, i) : __shfl_sync(kFull, fb, i - kQuantiles);
+        a0 = fmaf(bf16_to_f32(__ldg(w + kOffW1 + i * kHidden + lane)), x, a0);
+        a1 = fmaf(bf16_to_f32(__ldg(w + kOffW1 + i * kHidden + lane + 32)), x, a1);
+    }
+    a0 = fmaxf(a0, 0.f);
+    a1 = fmaxf(a1, 0.f);
+    float c0 = bf16_to_f32(__ldg(w + kOffB2 + lane)), c1 = bf16_to_f32(__ldg(w + kOffB2 + lane + 32));
+#pragma unroll 4
+    for (int k = 0; k < kHidden; ++k) {
+        const float x = k < 32 ? __shfl_sync(kFull, a0, k) : __shfl_sync(kFull, a1, k - 32);
+        c0 = fmaf(bf16_to_f32(__ldg(w + kOffW2 + k * kHidden + lane)), x, c0);
+        c1 = fmaf(bf16_to_f32(__ldg(w + kOffW2 + k * kHidden + lane + 32)), x, c1);
+    }
+    c0 = fmaxf(c0, 0.f);
+    c1 = fmaxf(c1, 0.f);
+    float o0 = bf16_to_f32(__ldg(w + kOffW3 + lane * 2)) * c0 + bf16_to_f32(__ldg(w + kOffW3 + (lane + 32) * 2)) * c1;
+    float o1 = bf16_to_f32(__ldg(w + kOffW3 + lane * 2 + 1)) * c0 +
+               bf16_to_f32(__ldg(w + kOffW3 + (lane + 32) * 2 + 1)) * c1;
+    for (int o = 16; o > 0; o >>= 1) {
+        o0 += __shfl_xor_sync(kFull, o0, o);
+        o1 += __shfl_xor_sync(kFull, o1, o);
+    }
+    return make_float2(o0 + bf16_to_f32(__ldg(w + kOffB3)), o1 + bf16_to_f32(__ldg(w + kOffB3 + 1)));
+}
+
+// Features of the seed window centred at box position (cu, cv): the tile's normalised value
+// quantiles (already in q[0..31]) and the ranks / N of the 3x3 pixels around the centre
+// (the centre's own rank where a neighbour lies outside the footprint).
+__device__ __forceinline__ void seed_features(const uint16_t* ord, int SP, const int* frow, int SH, int N, int cu,
+                                              int cv, const float* q, float* fa, float* fb) {
+    const int lane = threadIdx.x & 31;
+    *fa = q[lane];
+    float nb = 0.f;
+    if (lane < kNeigh) {
+        int u = cu + lane % 3 - 1, v = cv + lane / 3 - 1;
+        bool in = v >= 0 && v < SH;
+        if (in) {
+            const int fr = frow[v];
+            in = u >= span_lo(fr) && u <= span_hi(fr);
+        }
+        if (!in) {
+            u = cu;
+            v = cv;
+        }
+        nb = (float)ord[v * SP + u] / (float)N;
+    }
+    *fb = nb;
+}
+
 template <class T>
 __device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, int loc) {
     return reinterpret_cast<T*>(loc >= 0 ? smem + loc : gslice + (-(long long)loc - 1));
@@ -634,13 +694,74 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     const int target = P.rank;
     const int BH = TY / P.RB;      // band height
     const int GW = TX / P.G;       // seed spacing within a seed row
+    // feasible median ranks of any window of this tile (Fig. 10): [lof, hif]
+    const int lof = target, hif = N - P.n + target;
 
     // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
+    // (or, with a learned bracket, two exact counts at predicted ranks, then ballot refine)
     stamp(P, tile, 3, G);
+    const bool learned = P.model != nullptr;
+    float* quant = reinterpret_cast<float*>(misc);  // the sort's scan scratch is free from here on
+    if (learned || P.samples != nullptr) {
+        if (warp == 0) {  // normalised value quantiles of the footprint: C at N (j + 1/2) / 32
+            const int q = min(N - 1, (int)(((long long)N * (2 * lane + 1)) / (2 * kQuantiles)));
+            const uint32_t e = om[q];
+            const float v = (float)load_px<DT>(Img(P), gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
+            const float mid = __shfl_sync(kFull, v, kQuantiles / 2);
+            const float spread = __shfl_sync(kFull, v, 7 * kQuantiles / 8) - __shfl_sync(kFull, v, kQuantiles / 8);
+            const float z = (v - mid) / (spread > 0.f ? spread : 1.f);
+            quant[lane] = fminf(fmaxf(z, -8.f), 8.f);
+        }
+        G.sync();
+    }
     for (int sd = warp; sd < P.RB * P.G; sd += nwarps) {
         const int band = sd / P.G, g = sd % P.G;
         const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
         const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
+        float fa = 0.f, fb = 0.f;
+        if (learned || P.samples != nullptr) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+        if (learned) {
+            const float2 o = mlp_forward_warp(P.model, fa, fb);
+            const float sig = __expf(fminf(fmaxf(o.y, -8.f), 2.f)) * P.bracket_z;
+            const float span = (float)(hif - lof);
+            const int lo = clampi(__float2int_rn(lof + (o.x - sig) * span), 0, N - 1);
+            const int hi = clampi(__float2int_rn(lof + (o.x + sig) * span), lo, N - 1);
+            // one coalesced pass over the window: members below lo and at or below hi
+            int clo = 0, chi = 0;
+            for (int i = 0; i < P.nrows; ++i) {
+                const int sp = spans[i];
+                const uint16_t* row = ord + (cv + ymin + i) * SP + cu;
+                for (int dx = span_lo(sp) + lane; dx <= span_hi(sp); dx += 32) {
+                    const int r = row[dx];
+                    clo += r < lo;
+                    chi += r <= hi;
+                }
+            }
+            clo = __reduce_add_sync(kFull, clo);
+            chi = __reduce_add_sync(kFull, chi);
+            int pivot, cnt, kind;
+            if (target < clo) {            // below the bracket: walk down from lo
+                pivot = lo, cnt = clo, kind = 2;
+            } else if (target >= chi) {    // above the bracket: walk up from hi + 1
+                pivot = hi + 1, cnt = chi, kind = 3;
+            } else if (target - clo < chi - target) {  // inside: start from the nearer end
+                pivot = lo, cnt = clo, kind = 1;
+            } else {
+                pivot = hi + 1, cnt = chi, kind = 1;
+            }
+            const int m = ballot_select(om, N, pivot, cnt, target, cu - cx0, cv - cy0, member);
+            if (m < 0) set_status(FIM_ERR_INTERNAL);
+            if (lane == 0) {
+                med[t * TX + s] = (uint16_t)max(m, 0);
+                if (P.stats) {
+                    atomicAdd(P.stats + 0, 1ull);
+                    atomicAdd(P.stats + kind, 1ull);
+                    atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
+                }
+            }
+            __syncwarp();
+            continue;
+        }
         // one histogram per concurrently solved seed
         uint32_t* hw = shist + (nwarps >= P.RB * P.G ? sd : warp) * kSeedBins;
         for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
@@ -686,6 +807,21 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         const int m = ballot_select(om, N, bin << hist_shift, below, target, cu - cx0, cv - cy0, member);
         if (m < 0) set_status(FIM_ERR_INTERNAL);
         if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+        if (P.samples != nullptr) {  // training row: features and the exact median's place in [lof, hif]
+            unsigned int row = 0;
+            if (lane == 0) row = atomicAdd(P.sample_count, 1u);
+            row = __shfl_sync(kFull, row, 0);
+            if ((int)row < P.sample_cap) {
+                float* dst = P.samples + (size_t)row * (kFeatures + 1);
+                dst[lane] = fa;
+                if (lane < kNeigh) dst[kQuantiles + lane] = fb;
+                if (lane == 0) dst[kFeatures] = hif > lof ? (float)(max(m, 0) - lof) / (float)(hif - lof) : 0.5f;
+            }
+        }
+        if (P.stats != nullptr && lane == 0) {
+            atomicAdd(P.stats + 0, 1ull);
+            atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - (bin << hist_shift)));
+        }
         __syncwarp();
     }
     G.sync();
