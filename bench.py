@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=1024, help="rows of the image in the CPU oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batched comparison")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-bracket comparison")
+    ap.add_argument("--train-images", type=int, default=200)
     ap.add_argument("--profile-case", default=None, metavar="SIDE:R",
                     help="only run two launches on a SIDE x SIDE crop of the image at radius R (for ncu)")
     return ap.parse_args()
@@ -282,6 +284,94 @@ def batched_section(fim, torch, reps: int = 3):
 
 
 # ---------------------------------------------------------------------------------------------
+# learned seed bracket vs plain seeds (6000x4000x3 u16, r = 48)
+# ---------------------------------------------------------------------------------------------
+
+def learned_section(fim, torch, n_train: int = 200, reps: int = 3):
+    """Trains the rank-bracket network on seed windows of n_train photo-like 1024x1024 images
+    (labels: exact medians from the plain GPU path, spot-checked against the oracle), then
+    filters the three 6000x4000 planes with the plain and the learned seeds."""
+    import numpy as np
+
+    import datagen
+    import oracle
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    k = fim.fim_create_kernel_circle(48)
+    t0 = time.perf_counter()
+    cap = n_train * 4096
+    rows = torch.zeros((cap, fim.ROW), dtype=torch.float32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    checked = 0
+    for i in range(n_train):
+        img = datagen.torch_photo_u16(datagen.seed_for(4, 100 + i), 1024, 1024)
+        out = torch.empty_like(img)
+        fim.fim_collect_seed_samples(img.data_ptr(), out.data_ptr(), 1024, 1024, 2048, fim.FIM_U16, k,
+                                     rows.data_ptr(), cap, count.data_ptr(), sh)
+        if i < 4:  # labels come from the plain path: spot-check it against the oracle
+            torch.cuda.synchronize()
+            host = img.view(torch.int16).cpu().numpy().view(np.uint16)
+            res = out.view(torch.int16).cpu().numpy().view(np.uint16)
+            rng = np.random.default_rng(i)
+            xs, ys = rng.integers(0, 1024, 300), rng.integers(0, 1024, 300)
+            exp = oracle.median_points(host, oracle.disk_offsets(48), xs, ys)
+            if not np.array_equal(res[ys, xs], exp):
+                raise RuntimeError("plain path disagrees with the oracle on training image %d" % i)
+            checked += len(xs)
+    torch.cuda.synchronize()
+    n = min(int(count.item()), cap)
+    gen_s = time.perf_counter() - t0
+    perm = torch.randperm(n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    data = rows[:n][perm].contiguous()
+    n_val = n // 10
+    train, val = data[n_val:], data[:n_val]
+    model = fim.Model.create(seed=2025)
+    t0 = time.perf_counter()
+    loss = model.train(train.data_ptr(), train.shape[0], 12, 4096, 2e-3, sh)
+    z = model.calibrate(val.data_ptr(), n_val, 0.9, sh)
+    train_s = time.perf_counter() - t0
+    planes = [datagen.torch_photo_u16(datagen.seed_for(4, c), 4000, 6000) for c in range(3)]
+    out_p = [torch.empty_like(p) for p in planes]
+    out_l = [torch.empty_like(p) for p in planes]
+    st_p = torch.zeros(5, dtype=torch.int64, device="cuda")
+    st_l = torch.zeros(5, dtype=torch.int64, device="cuda")
+
+    def run(mdl, outs, stats=0):
+        for p, o in zip(planes, outs):
+            fim.fim_median_learned(p.data_ptr(), o.data_ptr(), 6000, 4000, 12000, fim.FIM_U16, k, mdl, sh, stats)
+
+    run(None, out_p, st_p.data_ptr())
+    run(model, out_l, st_l.data_ptr())
+    torch.cuda.synchronize()
+    same = all(torch.equal(a.view(torch.int16), b.view(torch.int16)) for a, b in zip(out_p, out_l))
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sum(ts) / len(ts)
+
+    ms_p = timed(lambda: run(None, out_p))
+    ms_l = timed(lambda: run(model, out_l))
+    sp, sl = st_p.cpu().numpy(), st_l.cpu().numpy()
+    mpix = 3 * 6000 * 4000 / 1e6
+    return {"workload": "6000x4000x3 u16 photo-like planes, disk r=48; trained on %d images 1024^2" % n_train,
+            "value": mpix / (ms_l * 1e-3), "unit": "Mpix/s", "plain_Mpix_s": mpix / (ms_p * 1e-3),
+            "speedup": ms_p / ms_l, "bit_exact_vs_plain": bool(same), "seeds": int(sl[0]),
+            "hit_rate": float(sl[1] / max(sl[0], 1)), "miss_below": int(sl[2]), "miss_above": int(sl[3]),
+            "seed_scan_ranks_plain": float(sp[4] / max(sp[0], 1)),
+            "seed_scan_ranks_learned": float(sl[4] / max(sl[0], 1)),
+            "train_rows": int(train.shape[0]), "val_rows": int(n_val), "final_loss": float(loss),
+            "bracket_z": float(z), "label_spot_checks": checked, "data_s": round(gen_s, 2),
+            "train_s": round(train_s, 2)}
+
+
+# ---------------------------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------------------------
 
@@ -463,6 +553,8 @@ def run_native(args):
     }
     if world == 1 and not args.no_batched:
         line["batched"] = batched_section(fim, torch)
+    if world == 1 and not args.no_learned:
+        line["learned"] = learned_section(fim, torch, args.train_images)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(img, args.cpu_rows)
     if rank == 0:

@@ -274,6 +274,7 @@ fim_status run_filter(const void* in, void* out, int w, int h, size_t pitch, int
         p->samples = samples;
         p->sample_count = count;
         p->sample_cap = cap;
+        get_phase_clock_buffer(&p->phase_clock, &p->phase_tiles);
         s = launch_tile_kernel(*p, st);
     }
     delete p;

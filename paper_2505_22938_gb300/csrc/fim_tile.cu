@@ -628,6 +628,71 @@ __device__ __forceinline__ void seed_features(const uint16_t* ord, int SP, const
     *fb = nb;
 }
 
+// Visits the ranks of every pixel of a window (row i of the kernel at ctr + (ymin + i) * SP,
+// ctr being the window centre's ordinal-image position shifted by ymin rows). Lane l takes
+// kernel rows l, l+32, ... and walks each from a lane-dependent column, so the 32 pixels
+// visited at once lie far apart (their ranks rarely share a histogram bin). Four ranks are
+// loaded before they are handed to `f`, so the loads of a group overlap instead of each
+// waiting behind the previous group's shared-memory atomics.
+template <class Fn>
+__device__ __forceinline__ void window_walk(const int* spans, int nrows, const uint16_t* ctr, int SP, Fn&& f) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < nrows; i += 32) {
+        const int sp = spans[i];
+        const int width = span_hi(sp) - span_lo(sp) + 1;
+        const uint16_t* row = ctr + i * SP + span_lo(sp);
+        int x = (lane * 37) % width;
+        int k = 0;
+        for (; k + 4 <= width; k += 4) {
+            int x1 = x + 1, x2 = x + 2, x3 = x + 3;
+            if (x1 >= width) x1 -= width;
+            if (x2 >= width) x2 -= width;
+            if (x3 >= width) x3 -= width;
+            const int r0 = row[x], r1 = row[x1], r2 = row[x2], r3 = row[x3];
+            f(r0);
+            f(r1);
+            f(r2);
+            f(r3);
+            x = x3 + 1 == width ? 0 : x3 + 1;
+        }
+        for (; k < width; ++k) {
+            f((int)row[x]);
+            x = (x + 1 == width) ? 0 : x + 1;
+        }
+    }
+}
+
+// Seed histogram (kSeedBins bins of one warp): the bin holding window-rank `target` when// Seed histogram (kSeedBins bins of one warp): the bin holding window-rank `target` when
+// `base` window members lie below bin 0. Returns the bin and, in *below, the members below it.
+__device__ __forceinline__ int hist_pick(const uint32_t* hw, int base, int target, int* below) {
+    const int lane = threadIdx.x & 31;
+    constexpr int per = kSeedBins / 32;
+    uint32_t local = 0;
+    for (int j = 0; j < per; ++j) local += hw[lane * per + j];
+    uint32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t tt = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += tt;
+    }
+    const int excl = base + (int)(incl - local);
+    const bool mine = excl <= target && target < base + (int)incl;
+    const uint32_t who = __ballot_sync(kFull, mine);
+    int bin = 0, run = 0;
+    if (mine) {
+        run = excl;
+        int j = 0;
+        for (; j < per - 1; ++j) {
+            const int c = (int)hw[lane * per + j];
+            if (run + c > target) break;
+            run += c;
+        }
+        bin = lane * per + j;
+    }
+    const int src = who ? __ffs(who) - 1 : 0;
+    *below = __shfl_sync(kFull, run, src);
+    return __shfl_sync(kFull, bin, src);
+}
+
 template <class T>
 __device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, int loc) {
     return reinterpret_cast<T*>(loc >= 0 ? smem + loc : gslice + (-(long long)loc - 1));
@@ -720,91 +785,53 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
         float fa = 0.f, fb = 0.f;
         if (learned || P.samples != nullptr) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+        // one histogram per concurrently solved seed
+        uint32_t* hw = shist + (nwarps >= P.RB * P.G ? sd : warp) * kSeedBins;
+        int pivot = -1, below = 0, kind = 0;
         if (learned) {
+            // Predicted bracket [lo, hi]; one coalesced pass counts the window below lo and at or
+            // below hi, and histograms only the ranks inside the bracket (fine bins, few atomics).
             const float2 o = mlp_forward_warp(P.model, fa, fb);
             const float sig = __expf(fminf(fmaxf(o.y, -8.f), 2.f)) * P.bracket_z;
             const float span = (float)(hif - lof);
             const int lo = clampi(__float2int_rn(lof + (o.x - sig) * span), 0, N - 1);
             const int hi = clampi(__float2int_rn(lof + (o.x + sig) * span), lo, N - 1);
-            // one coalesced pass over the window: members below lo and at or below hi
+            int hb = 0;
+            while (((hi - lo) >> hb) >= kSeedBins) ++hb;
+            for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+            __syncwarp();
             int clo = 0, chi = 0;
-            for (int i = 0; i < P.nrows; ++i) {
-                const int sp = spans[i];
-                const uint16_t* row = ord + (cv + ymin + i) * SP + cu;
-                for (int dx = span_lo(sp) + lane; dx <= span_hi(sp); dx += 32) {
-                    const int r = row[dx];
-                    clo += r < lo;
-                    chi += r <= hi;
-                }
-            }
+            window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
+                clo += r < lo;
+                chi += r <= hi;
+                if (r >= lo && r <= hi) atomicAdd(&hw[(r - lo) >> hb], 1u);
+            });
             clo = __reduce_add_sync(kFull, clo);
             chi = __reduce_add_sync(kFull, chi);
-            int pivot, cnt, kind;
-            if (target < clo) {            // below the bracket: walk down from lo
-                pivot = lo, cnt = clo, kind = 2;
-            } else if (target >= chi) {    // above the bracket: walk up from hi + 1
-                pivot = hi + 1, cnt = chi, kind = 3;
-            } else if (target - clo < chi - target) {  // inside: start from the nearer end
-                pivot = lo, cnt = clo, kind = 1;
-            } else {
-                pivot = hi + 1, cnt = chi, kind = 1;
-            }
-            const int m = ballot_select(om, N, pivot, cnt, target, cu - cx0, cv - cy0, member);
-            if (m < 0) set_status(FIM_ERR_INTERNAL);
-            if (lane == 0) {
-                med[t * TX + s] = (uint16_t)max(m, 0);
-                if (P.stats) {
-                    atomicAdd(P.stats + 0, 1ull);
-                    atomicAdd(P.stats + kind, 1ull);
-                    atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
-                }
-            }
             __syncwarp();
-            continue;
-        }
-        // one histogram per concurrently solved seed
-        uint32_t* hw = shist + (nwarps >= P.RB * P.G ? sd : warp) * kSeedBins;
-        for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
-        __syncwarp();
-        // Lane l takes kernel rows l, l+32, ... and walks each from a lane-dependent column,
-        // so the 32 pixels counted at once lie far apart and rarely share a histogram bin.
-        for (int i = lane; i < P.nrows; i += 32) {
-            const int sp = spans[i];
-            const int width = span_hi(sp) - span_lo(sp) + 1;
-            const uint16_t* row = ord + (cv + ymin + i) * SP + cu + span_lo(sp);
-            int x = (lane * 37) % width;
-            for (int k = 0; k < width; ++k) {
-                atomicAdd(&hw[row[x] >> hist_shift], 1u);
-                x = (x + 1 == width) ? 0 : x + 1;
+            if (clo <= target && target < chi) {
+                const int bin = hist_pick(hw, clo, target, &below);
+                pivot = lo + (bin << hb);
+                kind = 1;
+            } else if (target < clo) {  // below the bracket: walk down from lo
+                pivot = lo;
+                below = clo;
+                kind = 2;
+            } else {                    // above the bracket: walk up from hi + 1
+                pivot = hi + 1;
+                below = chi;
+                kind = 3;
             }
         }
-        __syncwarp();
-        uint32_t local = 0;
-        for (int j = 0; j < kSeedBins / 32; ++j) local += hw[lane * (kSeedBins / 32) + j];
-        uint32_t incl = local;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t tt = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += tt;
+        if (pivot < 0) {
+            for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+            __syncwarp();
+            window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
+                        [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
+            __syncwarp();
+            pivot = hist_pick(hw, 0, target, &below) << hist_shift;
         }
-        const uint32_t excl = incl - local;
-        const bool mine = (int)excl <= target && target < (int)incl;
-        const uint32_t who = __ballot_sync(kFull, mine);
-        int bin = 0, below = 0;
-        if (mine) {
-            uint32_t run = excl;
-            int j = 0;
-            for (; j < kSeedBins / 32 - 1; ++j) {
-                const uint32_t c = hw[lane * (kSeedBins / 32) + j];
-                if ((int)(run + c) > target) break;
-                run += c;
-            }
-            bin = lane * (kSeedBins / 32) + j;
-            below = (int)run;
-        }
-        const int src_lane = __ffs(who) - 1;
-        bin = __shfl_sync(kFull, bin, src_lane);
-        below = __shfl_sync(kFull, below, src_lane);
-        const int m = ballot_select(om, N, bin << hist_shift, below, target, cu - cx0, cv - cy0, member);
+        const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
         if (m < 0) set_status(FIM_ERR_INTERNAL);
         if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
         if (P.samples != nullptr) {  // training row: features and the exact median's place in [lof, hif]
@@ -820,7 +847,8 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         }
         if (P.stats != nullptr && lane == 0) {
             atomicAdd(P.stats + 0, 1ull);
-            atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - (bin << hist_shift)));
+            if (kind) atomicAdd(P.stats + kind, 1ull);
+            atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
         }
         __syncwarp();
     }
