@@ -167,7 +167,7 @@ int device_smem_limit() {
 }
 
 static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
-fim_status layout_plan(Plan* p, int smem_limit);
+fim_status layout_plan(Plan* p, int smem_limit, bool stage_model = false);
 
 static int elem_size(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); }
 
@@ -248,7 +248,13 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     return layout_plan(p, smem_limit);
 }
 
-fim_status layout_plan(Plan* p, int smem_limit) {
+fim_status plan_stage_model(Plan* p, int smem_limit) {
+    if (p->model == nullptr) return FIM_OK;
+    if (layout_plan(p, smem_limit, true) == FIM_OK) return FIM_OK;
+    return layout_plan(p, smem_limit, false);
+}
+
+fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
     const int Tx = p->Tx, Ty = p->Ty, SP = p->SP;
     const size_t omb = p->wide ? 4 : 2;      // omnigram entry / position bytes
     const size_t om_bytes = align16((size_t)p->N * omb);
@@ -265,6 +271,8 @@ fim_status layout_plan(Plan* p, int smem_limit) {
     take_tab(&p->off_htab, (size_t)p->nrows * 8);
     take_tab(&p->off_spans, (size_t)p->nrows * 4);
     take_tab(&p->off_frow, (size_t)p->SH * 4);
+    p->off_model = -1;
+    if (stage_model) take_tab(&p->off_model, (size_t)kMlpParams * 2);
     p->tab_bytes = (int)tab;  // everything from here on belongs to one tile group
     p->off_misc = (int)tab;
     tab += 256;

@@ -26,6 +26,7 @@ constexpr int kNeigh = 9;        // 3x3 neighbourhood ranks of the window centre
 constexpr int kFeatures = kQuantiles + kNeigh;
 constexpr int kHidden = 64;
 constexpr int kMlpParams = kFeatures * kHidden + kHidden + kHidden * kHidden + kHidden + kHidden * 2 + 2;
+static_assert(kMlpParams % 2 == 0, "parameters are staged as 32-bit pairs");
 // parameter offsets in the flat vector: W1[f][h], b1[h], W2[h][h'], b2[h'], W3[h'][2], b3[2]
 constexpr int kOffW1 = 0;
 constexpr int kOffB1 = kOffW1 + kFeatures * kHidden;
@@ -91,6 +92,7 @@ struct Plan {
     // Array placement. A location >= 0 is a byte offset into dynamic shared memory; a location
     // < 0 is -(offset + 1) into the CTA's slice of global scratch.
     int off_vtab, off_htab, off_spans, off_frow;   // tables (shared memory, whole kernel)
+    int off_model;                                  // bracket MLP parameters in shared memory, or -1
     int tab_bytes;                                  // the tables' extent; a tile group's partition follows
     int off_misc;                                   // 64 words of scan scratch (per group)
     int group_bytes;                                // bytes of one group's partition (smem_bytes - tab_bytes)
@@ -147,6 +149,9 @@ fim_status release_scratch();
 int device_sm_count();
 fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, int smem_limit,
                      Plan* p, int cta_threads = 0);
+// Re-lays out a plan whose model is set so that the bracket MLP's parameters are staged in
+// shared memory; keeps them in device memory (off_model = -1) when they do not fit.
+fim_status plan_stage_model(Plan* p, int smem_limit);
 fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int cta_threads = 0);
 int device_smem_limit();
 

@@ -270,6 +270,9 @@ fim_status run_filter(const void* in, void* out, int w, int h, size_t pitch, int
         p->pitch = (long long)pitch;
         p->model = md ? md->wb : nullptr;
         p->bracket_z = md ? md->bracket_z : 0.f;
+        s = plan_stage_model(p, limit);
+    }
+    if (s == FIM_OK) {
         p->stats = stats;
         p->samples = samples;
         p->sample_count = count;

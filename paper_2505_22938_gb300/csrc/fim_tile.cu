@@ -11,6 +11,8 @@
 //   2. ordinal image   - I(Omega[v]) = v (Eq. 4), exact 16-bit ranks.
 //   3. seed solve      - RB*G seed windows, one warp each: coarse histogram of I over the
 //                        window, then a ballot scan of Omega to the exact median (Sec. 4.2).
+//                        With a learned bracket (an extension), a block-wide MLP proposes a
+//                        rank bracket per seed and exact counts at its ends replace the histogram.
 //   4. seed rows       - one warp per (seed, direction) slides the window left/right; lanes
 //                        split the kernel rows and reduce the count change (Sec. 3.3 step 4).
 //   5. vertical sweep  - one thread per (column, band, direction) slides its window up or
@@ -243,8 +245,8 @@ __device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, in
 // scanning this is the cheapest schedule; the last few lanes of a warp (long jumps at edges and
 // impulses) are finished by warp-cooperative ballot scans instead of keeping 29+ lanes idle.
 // Same contract as ballot_select, per lane. All loops are bounded by the omnigram length.
-constexpr int kHandoff = 4;
-constexpr int kHandoffAfter = 16;  // groups
+constexpr int kHandoff = 8;
+constexpr int kHandoffAfter = 12;  // groups
 
 template <int SHAPE, int W>
 __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
@@ -302,9 +304,10 @@ __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restric
         const int nj = __shfl_sync(kFull, nextv, j);
         const int needj = __shfl_sync(kFull, need, j);
         const int pxj = __shfl_sync(kFull, px, j);
+        const int pyj = __shfl_sync(kFull, py, j);
         const int pj = upj ? nj : nj + 1;
         const int cj = upj ? target + 1 - needj : target + needj;
-        const int mj = ballot_select(om, N, pj, cj, target, pxj, py, member);
+        const int mj = ballot_select(om, N, pj, cj, target, pxj, pyj, member);
         if (lane == j) m = mj;
     }
     return m;
@@ -574,34 +577,34 @@ __device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_floa
 
 // Warp-cooperative forward pass of the bracket MLP (bf16 weights, fp32 accumulation). Lane l
 // holds feature l in fa (l < 32) and feature 32 + l in fb (l < 9). Returns (mu, s) in all lanes.
+// w is a generic pointer: the CTA's shared-memory copy of the parameters, or device memory.
 __device__ __forceinline__ float2 mlp_forward_warp(const uint16_t* __restrict__ w, float fa, float fb) {
     const int lane = threadIdx.x & 31;
-    float a0 = bf16_to_f32(__ldg(w + kOffB1 + lane)), a1 = bf16_to_f32(__ldg(w + kOffB1 + lane + 32));
+    float a0 = bf16_to_f32(w[kOffB1 + lane]), a1 = bf16_to_f32(w[kOffB1 + lane + 32]);
 #pragma unroll 4
     for (int i = 0; i < kFeatures; ++i) {
         const float x = i < kQuantiles ? __shfl_sync(kFull, fa, i) : __shfl_sync(kFull, fb, i - kQuantiles);
-        a0 = fmaf(bf16_to_f32(__ldg(w + kOffW1 + i * kHidden + lane)), x, a0);
-        a1 = fmaf(bf16_to_f32(__ldg(w + kOffW1 + i * kHidden + lane + 32)), x, a1);
+        a0 = fmaf(bf16_to_f32(w[kOffW1 + i * kHidden + lane]), x, a0);
+        a1 = fmaf(bf16_to_f32(w[kOffW1 + i * kHidden + lane + 32]), x, a1);
     }
     a0 = fmaxf(a0, 0.f);
     a1 = fmaxf(a1, 0.f);
-    float c0 = bf16_to_f32(__ldg(w + kOffB2 + lane)), c1 = bf16_to_f32(__ldg(w + kOffB2 + lane + 32));
+    float c0 = bf16_to_f32(w[kOffB2 + lane]), c1 = bf16_to_f32(w[kOffB2 + lane + 32]);
 #pragma unroll 4
     for (int k = 0; k < kHidden; ++k) {
         const float x = k < 32 ? __shfl_sync(kFull, a0, k) : __shfl_sync(kFull, a1, k - 32);
-        c0 = fmaf(bf16_to_f32(__ldg(w + kOffW2 + k * kHidden + lane)), x, c0);
-        c1 = fmaf(bf16_to_f32(__ldg(w + kOffW2 + k * kHidden + lane + 32)), x, c1);
+        c0 = fmaf(bf16_to_f32(w[kOffW2 + k * kHidden + lane]), x, c0);
+        c1 = fmaf(bf16_to_f32(w[kOffW2 + k * kHidden + lane + 32]), x, c1);
     }
     c0 = fmaxf(c0, 0.f);
     c1 = fmaxf(c1, 0.f);
-    float o0 = bf16_to_f32(__ldg(w + kOffW3 + lane * 2)) * c0 + bf16_to_f32(__ldg(w + kOffW3 + (lane + 32) * 2)) * c1;
-    float o1 = bf16_to_f32(__ldg(w + kOffW3 + lane * 2 + 1)) * c0 +
-               bf16_to_f32(__ldg(w + kOffW3 + (lane + 32) * 2 + 1)) * c1;
+    float o0 = bf16_to_f32(w[kOffW3 + lane * 2]) * c0 + bf16_to_f32(w[kOffW3 + (lane + 32) * 2]) * c1;
+    float o1 = bf16_to_f32(w[kOffW3 + lane * 2 + 1]) * c0 + bf16_to_f32(w[kOffW3 + (lane + 32) * 2 + 1]) * c1;
     for (int o = 16; o > 0; o >>= 1) {
         o0 += __shfl_xor_sync(kFull, o0, o);
         o1 += __shfl_xor_sync(kFull, o1, o);
     }
-    return make_float2(o0 + bf16_to_f32(__ldg(w + kOffB3)), o1 + bf16_to_f32(__ldg(w + kOffB3 + 1)));
+    return make_float2(o0 + bf16_to_f32(w[kOffB3]), o1 + bf16_to_f32(w[kOffB3 + 1]));
 }
 
 // Features of the seed window centred at box position (cu, cv): the tile's normalised value
@@ -779,78 +782,157 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         }
         G.sync();
     }
-    for (int sd = warp; sd < P.RB * P.G; sd += nwarps) {
-        const int band = sd / P.G, g = sd % P.G;
-        const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
-        const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
-        float fa = 0.f, fb = 0.f;
-        if (learned || P.samples != nullptr) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
-        // one histogram per concurrently solved seed
-        uint32_t* hw = shist + (nwarps >= P.RB * P.G ? sd : warp) * kSeedBins;
-        int pivot = -1, below = 0, kind = 0;
-        if (learned) {
-            // Predicted bracket [lo, hi]; one coalesced pass counts the window below lo and at or
-            // below hi, and histograms only the ranks inside the bracket (fine bins, few atomics).
-            const float2 o = mlp_forward_warp(P.model, fa, fb);
-            const float sig = __expf(fminf(fmaxf(o.y, -8.f), 2.f)) * P.bracket_z;
-            const float span = (float)(hif - lof);
-            const int lo = clampi(__float2int_rn(lof + (o.x - sig) * span), 0, N - 1);
-            const int hi = clampi(__float2int_rn(lof + (o.x + sig) * span), lo, N - 1);
-            int hb = 0;
-            while (((hi - lo) >> hb) >= kSeedBins) ++hb;
-            for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
-            __syncwarp();
-            int clo = 0, chi = 0;
-            window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
-                clo += r < lo;
-                chi += r <= hi;
-                if (r >= lo && r <= hi) atomicAdd(&hw[(r - lo) >> hb], 1u);
-            });
-            clo = __reduce_add_sync(kFull, clo);
-            chi = __reduce_add_sync(kFull, chi);
-            __syncwarp();
-            if (clo <= target && target < chi) {
-                const int bin = hist_pick(hw, clo, target, &below);
-                pivot = lo + (bin << hb);
-                kind = 1;
-            } else if (target < clo) {  // below the bracket: walk down from lo
-                pivot = lo;
-                below = clo;
-                kind = 2;
-            } else {                    // above the bracket: walk up from hi + 1
-                pivot = hi + 1;
-                below = chi;
-                kind = 3;
-            }
+    const int nseeds = P.RB * P.G;
+    static_assert(kHidden + kNeigh + 2 * kHidden <= kSeedBins, "MLP activations fit a seed histogram per seed");
+    if (learned) {
+        // Learned bracket (extension): the bracket MLP runs block-wide over a chunk of seeds
+        // (thread per (seed, hidden unit), activations in the seed-histogram buffers), then one
+        // warp per seed counts its window at the bracket ends, histograms the ranks inside the
+        // bracket finely, and scans Omega from the fine bin of the target (or, on a miss, from
+        // the bracket end the target lies beyond).
+        const uint16_t* wts =
+            P.off_model >= 0 ? reinterpret_cast<const uint16_t*>(smem_base + P.off_model) : P.model;
+        const int chunk_max = min(nwarps, nseeds);
+        // activations: 64 + chunk * (9 + 64 + 64) floats, within the chunk * 1 KiB of histograms
+        float* hbase = reinterpret_cast<float*>(shist);  // layer-1 pre-activation of the quantiles
+        float* xs = hbase + kHidden;                      // [chunk][kNeigh]
+        float* h1 = xs + chunk_max * kNeigh;              // [chunk][kHidden]
+        float* h2 = h1 + chunk_max * kHidden;             // [chunk][kHidden]
+        for (int j = tid; j < kHidden; j += nthreads) {
+            float h = bf16_to_f32(wts[kOffB1 + j]);
+            for (int i = 0; i < kQuantiles; ++i) h = fmaf(quant[i], bf16_to_f32(wts[kOffW1 + i * kHidden + j]), h);
+            hbase[j] = h;
         }
-        if (pivot < 0) {
+        for (int c0 = 0; c0 < nseeds; c0 += chunk_max) {
+            const int chunk = min(chunk_max, nseeds - c0);
+            if (warp < chunk) {
+                const int sd = c0 + warp;
+                const int band = sd / P.G, g = sd % P.G;
+                const int cu = g * GW + GW / 2 - xmin, cv = band * BH + BH / 2 - ymin;
+                float fa, fb;
+                seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+                if (lane < kNeigh) xs[warp * kNeigh + lane] = fb;
+            }
+            G.sync();
+            for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
+                const int sl = idx / kHidden, j = idx % kHidden;
+                float h = hbase[j];
+#pragma unroll
+                for (int i = 0; i < kNeigh; ++i)
+                    h = fmaf(xs[sl * kNeigh + i], bf16_to_f32(wts[kOffW1 + (kQuantiles + i) * kHidden + j]), h);
+                h1[idx] = fmaxf(h, 0.f);
+            }
+            G.sync();
+            for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
+                const int sl = idx / kHidden, j = idx % kHidden;
+                float h = bf16_to_f32(wts[kOffB2 + j]);
+#pragma unroll 8
+                for (int k = 0; k < kHidden; ++k) h = fmaf(h1[sl * kHidden + k], bf16_to_f32(wts[kOffW2 + k * kHidden + j]), h);
+                h2[idx] = fmaxf(h, 0.f);
+            }
+            G.sync();
+            int lo = 0, hi = 0;
+            if (warp < chunk) {  // output layer: lanes hold hidden units lane and lane + 32
+                const float x0 = h2[warp * kHidden + lane], x1 = h2[warp * kHidden + lane + 32];
+                float o0 = bf16_to_f32(wts[kOffW3 + lane * 2]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2]) * x1;
+                float o1 = bf16_to_f32(wts[kOffW3 + lane * 2 + 1]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2 + 1]) * x1;
+                for (int o = 16; o > 0; o >>= 1) {
+                    o0 += __shfl_xor_sync(kFull, o0, o);
+                    o1 += __shfl_xor_sync(kFull, o1, o);
+                }
+                o0 += bf16_to_f32(wts[kOffB3]);
+                o1 += bf16_to_f32(wts[kOffB3 + 1]);
+                const float sig = __expf(fminf(fmaxf(o1, -8.f), 2.f)) * P.bracket_z;
+                const float span = (float)(hif - lof);
+                lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
+                hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
+            }
+            G.sync();  // the histograms below overwrite the activations
+            if (warp < chunk) {
+                const int sd = c0 + warp;
+                const int band = sd / P.G, g = sd % P.G;
+                const int s = g * GW + GW / 2, t = band * BH + BH / 2;
+                const int cu = s - xmin, cv = t - ymin;
+                // One pass counts the window below lo and at or below hi and histograms the ranks
+                // inside [lo, hi] in kFineBins fine bins. Every pixel makes one atomic: pixels
+                // outside the bracket add to a lane-private spare word (its own bank), so the
+                // bracket's few pixels are the only ones that can collide.
+                constexpr int kFineBins = kSeedBins - 32;
+                int hb = 0;
+                while (((hi - lo) >> hb) >= kFineBins) ++hb;
+                uint32_t* hw = shist + warp * kSeedBins;
+                for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+                __syncwarp();
+                int clo = 0, chi = 0;
+                window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
+                    clo += r < lo;
+                    chi += r <= hi;
+                    const bool in = (unsigned)(r - lo) <= (unsigned)(hi - lo);
+                    atomicAdd(&hw[in ? (r - lo) >> hb : kFineBins + lane], 1u);
+                });
+                clo = __reduce_add_sync(kFull, clo);
+                chi = __reduce_add_sync(kFull, chi);
+                __syncwarp();
+                int pivot, below, kind;
+                if (target < clo) {         // below the bracket: walk down from lo
+                    pivot = lo;
+                    below = clo;
+                    kind = 2;
+                } else if (target >= chi) { // above the bracket: walk up from hi + 1
+                    pivot = hi + 1;
+                    below = chi;
+                    kind = 3;
+                } else {                    // inside: the fine bin holding the target (the spare
+                    kind = 1;               // words come after every fine bin, so are not reached)
+                    pivot = lo + (hist_pick(hw, clo, target, &below) << hb);
+                }
+                const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+                if (m < 0) set_status(FIM_ERR_INTERNAL);
+                if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+                if (P.stats != nullptr && lane == 0) {
+                    atomicAdd(P.stats + 0, 1ull);
+                    atomicAdd(P.stats + kind, 1ull);
+                    atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
+                }
+            }
+            G.sync();  // the next chunk reuses the activation buffers
+        }
+    } else {
+        for (int sd = warp; sd < nseeds; sd += nwarps) {
+            const int band = sd / P.G, g = sd % P.G;
+            const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
+            const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
+            float fa = 0.f, fb = 0.f;
+            if (P.samples != nullptr) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+            // one histogram per concurrently solved seed
+            uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
             for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
             __syncwarp();
             window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
                         [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
             __syncwarp();
-            pivot = hist_pick(hw, 0, target, &below) << hist_shift;
-        }
-        const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
-        if (m < 0) set_status(FIM_ERR_INTERNAL);
-        if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
-        if (P.samples != nullptr) {  // training row: features and the exact median's place in [lof, hif]
-            unsigned int row = 0;
-            if (lane == 0) row = atomicAdd(P.sample_count, 1u);
-            row = __shfl_sync(kFull, row, 0);
-            if ((int)row < P.sample_cap) {
-                float* dst = P.samples + (size_t)row * (kFeatures + 1);
-                dst[lane] = fa;
-                if (lane < kNeigh) dst[kQuantiles + lane] = fb;
-                if (lane == 0) dst[kFeatures] = hif > lof ? (float)(max(m, 0) - lof) / (float)(hif - lof) : 0.5f;
+            int below = 0;
+            const int pivot = hist_pick(hw, 0, target, &below) << hist_shift;
+            const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+            if (m < 0) set_status(FIM_ERR_INTERNAL);
+            if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+            if (P.samples != nullptr) {  // training row: features and the exact median's place in [lof, hif]
+                unsigned int row = 0;
+                if (lane == 0) row = atomicAdd(P.sample_count, 1u);
+                row = __shfl_sync(kFull, row, 0);
+                if ((int)row < P.sample_cap) {
+                    float* dst = P.samples + (size_t)row * (kFeatures + 1);
+                    dst[lane] = fa;
+                    if (lane < kNeigh) dst[kQuantiles + lane] = fb;
+                    if (lane == 0) dst[kFeatures] = hif > lof ? (float)(max(m, 0) - lof) / (float)(hif - lof) : 0.5f;
+                }
             }
+            if (P.stats != nullptr && lane == 0) {
+                atomicAdd(P.stats + 0, 1ull);
+                atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
+            }
+            __syncwarp();
         }
-        if (P.stats != nullptr && lane == 0) {
-            atomicAdd(P.stats + 0, 1ull);
-            if (kind) atomicAdd(P.stats + kind, 1ull);
-            atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
-        }
-        __syncwarp();
     }
     G.sync();
 
@@ -865,15 +947,24 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         int cu = s - xmin;
         const int cv = t - ymin;
         int p = med[t * TX + s];
+        constexpr int kRowsPerLane = (kMaxExtent + 31) / 32;
+        int eo[kRowsPerLane], lo[kRowsPerLane];  // this lane's rows: entering / leaving offsets
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) {
+            const int i = lane + 32 * q;
+            eo[q] = lo[q] = 0;  // rows beyond the kernel compare the centre with itself: no change
+            if (i < P.nrows) {
+                const int2 o = htab[i];
+                eo[q] = right ? o.y : o.x - 1;
+                lo[q] = right ? o.x : o.y - 1;
+            }
+        }
         for (int k = 0; k < steps; ++k) {
             const uint16_t* ctr = ord + cv * SP + cu;
             int d = 0;
-            for (int i = lane; i < P.nrows; i += 32) {
-                const int2 o = htab[i];
-                const int e = right ? o.y : o.x - 1;
-                const int l = right ? o.x : o.y - 1;
-                d += (int)(ctr[e] < p) - (int)(ctr[l] < p);
-            }
+#pragma unroll
+            for (int q = 0; q < kRowsPerLane; ++q)
+                if (32 * q < P.nrows) d += (int)(ctr[eo[q]] < p) - (int)(ctr[lo[q]] < p);
             d = __reduce_add_sync(kFull, d);
             cu += right ? 1 : -1;
             s += right ? 1 : -1;
@@ -957,6 +1048,11 @@ __device__ __forceinline__ void load_tables(const Plan& P) {
         spans[i] = P.spans[i];
     }
     for (int i = tid; i < P.SH; i += nt) frow[i] = P.frow[i];
+    if (P.off_model >= 0 && P.model != nullptr) {  // kMlpParams is even: copy 32-bit pairs
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(P.model);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(smem + P.off_model);
+        for (int i = tid; i < kMlpParams / 2; i += nt) dst[i] = src[i];
+    }
 }
 
 // Persistent CTAs: each takes tiles from the queue counter in the scratch header until none are
