@@ -200,6 +200,11 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->ncols = k->xmax - k->xmin + 1;
     p->n = k->n;
     p->rank = rank;
+    // Small kernels: a warp's 32 chains drawn from every band even out the per-warp work of the
+    // vertical sweep (scan lengths follow the image content of a band); large kernels prefer the
+    // shorter per-step divergence of 32 adjacent columns of one band (measured on the 4096^2
+    // photo-like workload: mixing gains 4-13 % up to r = 16, loses 2-4 % from r = 32 on).
+    p->vmix = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1 <= 40 ? 1 : 0;
     p->S = ts.Tx + (k->xmax - k->xmin);
     p->SH = ts.Ty + (k->ymax - k->ymin);
     if (p->S > kMaxSide || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
@@ -242,6 +247,9 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
         p->spans[i] = (int)((uint32_t)(k->rlo[i] & 0xffff) | ((uint32_t)k->rhi[i] << 16));
     }
     p->sort = dtype == FIM_U8 ? kSortCount8 : (dtype == FIM_U16 ? kSortCount16 : kSortRadix);
+    // The 65536 bins of the 16-bit counting sort (128 KiB) leave room for one CTA per SM, which
+    // only a full 1024-thread CTA uses well; smaller CTAs sort 16-bit data by two radix passes.
+    if (dtype == FIM_U16 && p->threads < 1024) p->sort = kSortRadix;
     // Placement. Tables, the ordinal image, medians and histograms always live in shared memory;
     // the omnigram, the radix keys and the radix position lists go to the CTA's global scratch
     // slice when shared memory cannot hold them (large kernels).
@@ -361,8 +369,8 @@ static bool parse_tile_env(TileShape* ts) {
 }
 
 fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int cta_threads) {
-    static const TileShape cands[] = {{64, 128, 8, 2}, {64, 64, 8, 2}, {32, 64, 8, 2}, {32, 32, 8, 2},
-                                      {32, 16, 8, 2}};
+    static const TileShape cands[] = {{32, 32, 2, 1}, {64, 128, 8, 2}, {64, 64, 8, 2}, {32, 64, 8, 2},
+                                      {32, 32, 8, 2}, {32, 16, 8, 2}};
     TileShape forced;
     if (parse_tile_env(&forced)) {  // explicit override (experiments, tuning)
         Plan* p = new (std::nothrow) Plan;
@@ -387,11 +395,14 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
             return FIM_OK;
         }
     }
-    // Taller tiles halve the seed and seed-row work per pixel but enlarge the footprint, which
-    // lengthens every refinement scan; they pay off once the kernel is large (measured on the
-    // 4096^2 photo-like workload: 64x128 is best from r = 48 on, 64x64 below).
+    // Defaults measured on the 4096^2 photo-like workload. Kernels up to 25 pixels across (33
+    // for 8-bit data): small tiles (the footprint, and so every refinement scan, shrinks with
+    // the tile) in 128-thread CTAs, many per SM (16-bit data then sorts by radix passes); up to
+    // 80 across: 64x64 tiles in 1024-thread CTAs; beyond: taller 64x128 tiles, which halve the
+    // seed and seed-row work per pixel.
     const int extent = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1;
-    const int first = extent >= 81 ? 0 : 1;
+    const int small_limit = dtype == FIM_U8 ? 33 : 25;
+    const int first = extent <= small_limit ? 0 : (extent >= 81 ? 1 : 2);
     for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
         const TileShape& c = cands[i];
         Plan* p = new (std::nothrow) Plan;

@@ -48,7 +48,7 @@ struct TileShape {
 enum SortKind : int {
     kSortCount8 = 0,   // 256-bin counting sort (8-bit data)
     kSortCount16 = 1,  // 65536-bin counting sort with packed 16-bit bins (16-bit data, Eq. 5)
-    kSortRadix = 2     // stable LSD radix sort, four 8-bit passes (32-bit float keys)
+    kSortRadix = 2     // stable LSD radix sort, 8-bit passes (four for float keys, two for 16-bit data)
 };
 
 // Everything a tile kernel launch needs, passed by value as a __grid_constant__ parameter.
@@ -64,6 +64,7 @@ struct Plan {
     int Tx, Ty, txshift, RB, G;
     int threads, nwarps;    // CTA size (all cooperative loops and per-warp buffers)
     int vthreads;           // 2*Tx*RB: threads of the vertical sweep (the first ones of the CTA)
+    int vmix;               // 1: the lanes of a vertical-sweep warp take their columns from all bands
     int S, SH;              // footprint bounding box (columns, rows)
     int SP;                 // row pitch (elements) of the ordinal image; SP/2 is odd
     int tiles_x, tiles_y;

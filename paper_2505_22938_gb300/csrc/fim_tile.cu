@@ -443,8 +443,8 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
     }
 }
 
-// Stable LSD radix ordinal transform for 32-bit keys (float data): four 8-bit passes over
-// bounding-box positions. Each warp owns one contiguous segment of the current order; a
+// Stable LSD radix ordinal transform: 8-bit passes over bounding-box positions, four for
+// 32-bit float keys, two for 16-bit data. Each warp owns one contiguous segment of the current order; a
 // pixel's new place is its (digit, warp)-major exclusive offset plus its position among
 // equal digits earlier in the segment (warp match). Histograms are laid out warp-major with
 // a pad word so that the leaders of one warp never share a bank. The sorted positions end in
@@ -467,7 +467,9 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     const int area = S * P.SH;
     const Pos* src = nullptr;
     Pos* dst = bufA;
-    for (int pass = 0; pass < 4; ++pass) {
+    constexpr int kPasses = DT == FIM_F32 ? 4 : 2;  // 8-bit digits of 32- or 16-bit keys
+    static_assert(kPasses % 2 == 0, "the sorted positions must end in list B");
+    for (int pass = 0; pass < kPasses; ++pass) {
         const int shift = 8 * pass;
         const int len = pass == 0 ? area : P.N;
         const int seg = ((len + nwarps - 1) / nwarps + 31) & ~31;
@@ -562,7 +564,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
         src = dst;
         dst = (dst == bufA) ? bufB : bufA;
     }
-    // four passes: the sorted positions are in B; rewrite them in place as omnigram entries
+    // an even number of passes: the sorted positions are in B; rewrite them in place as entries
     typename Loc<W>::E* om = reinterpret_cast<typename Loc<W>::E*>(bufB);
     for (int v = tid; v < P.N; v += nthreads) {
         const int pos = (int)bufB[v];
@@ -574,38 +576,6 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
 // ---- learned rank bracket (seed windows) ---------------------------------------------------
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
-
-// Warp-cooperative forward pass of the bracket MLP (bf16 weights, fp32 accumulation). Lane l
-// holds feature l in fa (l < 32) and feature 32 + l in fb (l < 9). Returns (mu, s) in all lanes.
-// w is a generic pointer: the CTA's shared-memory copy of the parameters, or device memory.
-__device__ __forceinline__ float2 mlp_forward_warp(const uint16_t* __restrict__ w, float fa, float fb) {
-    const int lane = threadIdx.x & 31;
-    float a0 = bf16_to_f32(w[kOffB1 + lane]), a1 = bf16_to_f32(w[kOffB1 + lane + 32]);
-#pragma unroll 4
-    for (int i = 0; i < kFeatures; ++i) {
-        const float x = i < kQuantiles ? __shfl_sync(kFull, fa, i) : __shfl_sync(kFull, fb, i - kQuantiles);
-        a0 = fmaf(bf16_to_f32(w[kOffW1 + i * kHidden + lane]), x, a0);
-        a1 = fmaf(bf16_to_f32(w[kOffW1 + i * kHidden + lane + 32]), x, a1);
-    }
-    a0 = fmaxf(a0, 0.f);
-    a1 = fmaxf(a1, 0.f);
-    float c0 = bf16_to_f32(w[kOffB2 + lane]), c1 = bf16_to_f32(w[kOffB2 + lane + 32]);
-#pragma unroll 4
-    for (int k = 0; k < kHidden; ++k) {
-        const float x = k < 32 ? __shfl_sync(kFull, a0, k) : __shfl_sync(kFull, a1, k - 32);
-        c0 = fmaf(bf16_to_f32(w[kOffW2 + k * kHidden + lane]), x, c0);
-        c1 = fmaf(bf16_to_f32(w[kOffW2 + k * kHidden + lane + 32]), x, c1);
-    }
-    c0 = fmaxf(c0, 0.f);
-    c1 = fmaxf(c1, 0.f);
-    float o0 = bf16_to_f32(w[kOffW3 + lane * 2]) * c0 + bf16_to_f32(w[kOffW3 + (lane + 32) * 2]) * c1;
-    float o1 = bf16_to_f32(w[kOffW3 + lane * 2 + 1]) * c0 + bf16_to_f32(w[kOffW3 + (lane + 32) * 2 + 1]) * c1;
-    for (int o = 16; o > 0; o >>= 1) {
-        o0 += __shfl_xor_sync(kFull, o0, o);
-        o1 += __shfl_xor_sync(kFull, o1, o);
-    }
-    return make_float2(o0 + bf16_to_f32(w[kOffB3]), o1 + bf16_to_f32(w[kOffB3 + 1]));
-}
 
 // Features of the seed window centred at box position (cu, cv): the tile's normalised value
 // quantiles (already in q[0..31]) and the ranks / N of the 3x3 pixels around the centre
@@ -733,12 +703,14 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
 
     // ---- 1. ordinal transform ------------------------------------------------------------------
     stamp(P, tile, 1, G);
-    if constexpr (DT == FIM_F32)
+    // float data always takes the radix sort; 16-bit data takes it in small CTAs, where the
+    // counting sort's 65536 bins would keep other CTAs off the SM
+    if (DT == FIM_F32 || (DT == FIM_U16 && P.sort == kSortRadix))
         ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
                                        place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
                                        place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
                                        reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, gx0, gy0, G);
-    else
+    else if constexpr (DT != FIM_F32)
         ordinal_transform_count<DT, W>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), misc, om, gx0, gy0,
                                        G);
     G.sync();
@@ -982,7 +954,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         const int groups = TX / 32;
         const int cg = warp % groups;
         const int rest = warp / groups;
-        const int band = rest % P.RB;
+        const int band = P.vmix ? (rest + lane) % P.RB : rest % P.RB;  // per lane with mixing
         const int down = rest / P.RB;  // 0: up, 1: down
         const int s = cg * 32 + lane;
         int t = band * BH + BH / 2;

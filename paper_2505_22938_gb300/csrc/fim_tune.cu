@@ -114,17 +114,17 @@ void tuned_clear() {
 }
 
 // Candidate tile configurations: tile width 32 or 64 (a warp row of the vertical sweep is 32
-// columns), tile height 16..128, bands of 1..16 rows, 1..4 seeds per seed row.
+// columns), tile height 16..128, 2..16 bands of at least 4 rows, 1..4 seeds per seed row.
 void tile_candidates(std::vector<TileShape>* out) {
     static const int txs[] = {64, 32};
     static const int tys[] = {128, 64, 32, 16};
-    static const int rbs[] = {4, 8, 16};
+    static const int rbs[] = {2, 4, 8, 16};
     static const int gs[] = {1, 2, 4};
     for (int tx : txs)
         for (int ty : tys)
             for (int rb : rbs)
                 for (int g : gs) {
-                    if (2 * tx * rb > 1024 || ty % rb != 0 || tx % g != 0) continue;
+                    if (2 * tx * rb > 1024 || ty % rb != 0 || ty / rb < 4 || tx % g != 0) continue;
                     out->push_back(TileShape{tx, ty, rb, g});
                 }
 }

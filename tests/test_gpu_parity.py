@@ -38,6 +38,16 @@ def test_u16_photo_crops(r):
     run_case(np.ascontiguousarray(img), "circle", r)
 
 
+@pytest.mark.parametrize("tile", ["64,64,8,2", "32,32,2,1", "32,16,2,2", "64,32,4,2"])
+@pytest.mark.parametrize("r", [3, 8, 20])
+def test_u16_sort_paths(tile, r, monkeypatch):
+    """16-bit data sorts by the 65536-bin counting sort in 1024-thread CTAs and by two radix
+    passes in smaller CTAs; both must give the oracle's result on the same crop."""
+    monkeypatch.setenv("FIM_TILE", tile)
+    img = datagen.config2_image(4096, 4096)[1500:1500 + 131, 700:700 + 149]
+    run_case(np.ascontiguousarray(img), "circle", r)
+
+
 @pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
 @pytest.mark.parametrize("r", [5, 21])
 def test_dtypes_ragged(dtype, r):
