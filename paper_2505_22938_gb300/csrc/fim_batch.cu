@@ -1,7 +1,8 @@
-// Batched persistent launch (host side): many images of any size, dtype and kernel share one
-// queue of tiles and one kernel launch. The batch object owns its device-side plans, the tile
-// prefix table and its workspace, so fim_batch_run() only zeroes the queue counter and launches:
-// both are stream operations and can be captured in a CUDA graph.
+// Batched persistent launch (host side): many images of any size, dtype and kernel in one
+// kernel launch. The batch object owns its device-side plans (sorted by decreasing cost per
+// tile) and its workspace, whose header holds one tile counter per job; fim_batch_run() only
+// zeroes the header and launches: both are stream operations and can be captured in a CUDA
+// graph.
 #include <string.h>
 
 #include <algorithm>
@@ -15,11 +16,10 @@ using namespace fim;
 
 struct fim_batch {
     int njobs = 0;
-    int total_tiles = 0, total_items = 0, max_groups = 1;
+    int total_tiles = 0, max_groups = 1, header_bytes = 256;
     int grid = 0, threads = 0, smem = 0;
     long long scratch_per_cta = 0;
     Plan* d_plans = nullptr;
-    int* d_prefix = nullptr;
     unsigned char* scratch = nullptr;
     int device = 0;
 };
@@ -39,7 +39,6 @@ void free_batch(fim_batch* b) {
     if (!b) return;
     cudaDeviceSynchronize();
     if (b->d_plans) cudaFree(b->d_plans);
-    if (b->d_prefix) cudaFree(b->d_prefix);
     if (b->scratch) cudaFree(b->scratch);
     delete b;
 }
@@ -76,58 +75,51 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
         p.pitch = (long long)j.pitch_bytes;
         p.ntiles = p.tiles_x * p.tiles_y;
         // as many groups as fit the CTA and shared memory, but no more than the job has tiles
-        int groups = kCta / p.threads;
+        int groups = std::min(kCta / p.threads, kMaxBatchGroups);
         while (groups > 1 && p.tab_bytes + (size_t)groups * p.group_bytes > (size_t)limit) --groups;
         p.groups = std::max(1, std::min(groups, p.ntiles));
     }
     std::vector<int> order((size_t)count);
     std::iota(order.begin(), order.end(), 0);
-    // an item's groups run side by side, so an item lasts about one tile of its job
+    // the CTAs visit the jobs in this order: expensive tiles first, cheap ones fill the tail
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return tile_cost(plans[a]) > tile_cost(plans[b]); });
     std::vector<Plan> sorted((size_t)count);
-    std::vector<int> prefix((size_t)count + 1, 0);
-    long long items = 0, tiles = 0, spc = 0;
+    long long tiles = 0, spc = 0;
     int smem = 0, max_groups = 1;
     for (int i = 0; i < count; ++i) {
         Plan& p = sorted[i];
         p = plans[order[i]];
-        prefix[i] = (int)items;
-        items += (p.ntiles + p.groups - 1) / p.groups;
         tiles += p.ntiles;
         spc = std::max(spc, p.scratch_per_cta);
         smem = std::max(smem, p.tab_bytes + p.groups * p.group_bytes);
         max_groups = std::max(max_groups, p.groups);
     }
-    if (items > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
-    prefix[count] = (int)items;
+    if (tiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
     fim_batch* b = new (std::nothrow) fim_batch();
     if (!b) return FIM_ERR_OOM;
     cudaGetDevice(&b->device);
     b->njobs = count;
     b->total_tiles = (int)tiles;
-    b->total_items = (int)items;
     b->max_groups = max_groups;
     b->scratch_per_cta = spc;
     b->threads = kCta;
     b->smem = smem;
+    b->header_bytes = (int)((((size_t)count * 4) + 255) & ~(size_t)255);
     fim_status s = batch_prepare(smem);
-    if (s == FIM_OK) s = batch_grid(b->threads, b->smem, items, &b->grid);
+    if (s == FIM_OK) s = batch_grid(b->threads, b->smem, tiles, &b->grid);
     if (s != FIM_OK) {
         free_batch(b);
         return s;
     }
-    const size_t scratch_bytes = 256 + (size_t)b->grid * (size_t)max_groups * (size_t)spc;
+    const size_t scratch_bytes = (size_t)b->header_bytes + (size_t)b->grid * (size_t)max_groups * (size_t)spc;
     if (cudaMalloc(&b->d_plans, sizeof(Plan) * (size_t)count) != cudaSuccess ||
-        cudaMalloc(&b->d_prefix, sizeof(int) * ((size_t)count + 1)) != cudaSuccess ||
         cudaMalloc(&b->scratch, scratch_bytes) != cudaSuccess) {
         cudaGetLastError();
         free_batch(b);
         return FIM_ERR_OOM;
     }
-    if (cudaMemcpy(b->d_plans, sorted.data(), sizeof(Plan) * (size_t)count, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_prefix, prefix.data(), sizeof(int) * ((size_t)count + 1), cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
+    if (cudaMemcpy(b->d_plans, sorted.data(), sizeof(Plan) * (size_t)count, cudaMemcpyHostToDevice) != cudaSuccess) {
         free_batch(b);
         return FIM_ERR_CUDA;
     }
@@ -139,9 +131,8 @@ fim_status fim_batch_run(fim_batch* b, void* stream) {
     if (!b) return FIM_ERR_INVALID_ARG;
     BatchArgs a;
     a.plans = b->d_plans;
-    a.item_prefix = b->d_prefix;
     a.njobs = b->njobs;
-    a.total_items = b->total_items;
+    a.header_bytes = b->header_bytes;
     a.max_groups = b->max_groups;
     a.scratch = b->scratch;
     a.scratch_per_cta = b->scratch_per_cta;

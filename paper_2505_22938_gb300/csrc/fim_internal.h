@@ -119,14 +119,16 @@ struct Plan {
 constexpr size_t kPlanScalarBytes = ((offsetof(Plan, frow) + 15) / 16) * 16;
 static_assert(offsetof(Plan, frow) % 4 == 0, "plan scalars are copied as 32-bit words");
 
+// Tile groups per batch CTA: each has its own named barrier, 1..15 (0 is the whole CTA).
+constexpr int kMaxBatchGroups = 15;
+
 // Arguments of the batched persistent launch (plans live in device memory).
 struct BatchArgs {
-    const Plan* plans;          // njobs plans, device memory
-    const int* item_prefix;     // njobs + 1 prefix sums of queue items (groups tiles each)
+    const Plan* plans;          // njobs plans, device memory, in the order the CTAs visit them
     int njobs;
-    int total_items;
+    int header_bytes;           // scratch header: one tile counter per job (zeroed before launch)
     int max_groups;             // group slots per CTA in the scratch layout
-    unsigned char* scratch;     // header (256 B: queue counter) + grid * max_groups * scratch_per_cta
+    unsigned char* scratch;     // header + grid * max_groups * scratch_per_cta
     long long scratch_per_cta;
 };
 
@@ -169,9 +171,10 @@ void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 // Device launch (fim_tile.cu).
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_device_status(cudaStream_t stream);
+fim_status read_and_clear_batch_status();  // (fim_batch_kernel.cu) called by the above after its sync
 fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
 fim_status batch_prepare(int smem);
-fim_status batch_grid(int threads, int smem, long long total_items, int* grid);
+fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);
 fim_status batch_launch(const BatchArgs& a, int grid, int threads, int smem, cudaStream_t stream);
 
 }  // namespace fim

@@ -1,0 +1,1033 @@
+#pragma once
+// Per-tile median kernel: each CTA takes Tx x Ty output tiles from a device-side queue and
+// filters them one after the other (Sec. 3.3, Sec. 4.2).
+//
+// Phases of one tile, separated by __syncthreads():
+//   1. ordinal transform - the rounded-rectangle footprint (Fig. 10) is read with clamp-to-edge
+//                        and key-value sorted by value, giving the omnigram Omega (Sec. 3.3):
+//                          8/16-bit data: counting sort over 256 / 65536 shared-memory bins, the
+//                                         bucket construction of Eq. 5 run by all threads;
+//                          float data:    stable LSD radix sort of order-preserving keys
+//                                         (Sec. 4.1 float key), four 8-bit passes.
+//   2. ordinal image   - I(Omega[v]) = v (Eq. 4), exact 16-bit ranks.
+//   3. seed solve      - RB*G seed windows, one warp each: coarse histogram of I over the
+//                        window, then a ballot scan of Omega to the exact median (Sec. 4.2).
+//                        With a learned bracket (an extension), a block-wide MLP proposes a
+//                        rank bracket per seed and exact counts at its ends replace the histogram.
+//   4. seed rows       - one warp per (seed, direction) slides the window left/right; lanes
+//                        split the kernel rows and reduce the count change (Sec. 3.3 step 4).
+//   5. vertical sweep  - one thread per (column, band, direction) slides its window up or
+//                        down (Fig. 7) and refines it by scanning Omega itself; the last few
+//                        lanes of a warp hand their long scans to warp ballots (Sec. 4.1, Eq. 2).
+//   6. output          - out = C[m] through the omnigram: the input value at Omega[m].
+// Pivots are exact previous medians (Huang's choice, Sec. 3.1): after each solve the count
+// below the pivot is exactly the target rank, and a slide only adds the change.
+//
+// W selects the omnigram encoding: W = 0 packs a location as two int8 coordinates (footprint
+// box up to 256 x 256, Sec. 4.1); W = 1 uses two int16 coordinates for larger boxes. OG = 1
+// keeps the omnigram in the CTA's global scratch slice when shared memory cannot hold it.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "fim_internal.h"
+
+namespace fim {
+namespace {
+
+// First device-side error since the last fim_sync_status(). Each translation unit that includes
+// this file has its own word (internal linkage); the host reads and clears all of them.
+__device__ int g_status;
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int DT>
+struct Traits;
+template <>
+struct Traits<FIM_U8> {
+    using T = uint8_t;
+    __device__ static uint32_t key(T v) { return v; }
+};
+template <>
+struct Traits<FIM_U16> {
+    using T = uint16_t;
+    __device__ static uint32_t key(T v) { return v; }
+};
+template <>
+struct Traits<FIM_F32> {
+    using T = float;
+    // Sign-magnitude to unsigned order (Sec. 4.1): negative values have all bits flipped,
+    // non-negative values only the sign bit, so unsigned comparison is IEEE totalOrder.
+    __device__ static uint32_t key(T v) {
+        const uint32_t b = __float_as_uint(v);
+        return b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
+    }
+};
+
+// Omnigram entry encodings (locations relative to the footprint box centre cx0, cy0).
+template <int W>
+struct Loc;
+template <>
+struct Loc<0> {
+    using E = uint16_t;    // entry
+    using Pos = uint16_t;  // bounding-box position in the radix lists
+    static constexpr int kGroup = 8;  // entries per 128-bit load
+    __device__ static E pack(int u, int v, int cx0, int cy0) {
+        return (E)((uint32_t)(uint8_t)(int8_t)(u - cx0) | ((uint32_t)(uint8_t)(int8_t)(v - cy0) << 8));
+    }
+    __device__ static int x(uint32_t e) { return (int)(int8_t)(e & 0xffu); }
+    __device__ static int y(uint32_t e) { return (int)(int8_t)((e >> 8) & 0xffu); }
+};
+template <>
+struct Loc<1> {
+    using E = uint32_t;
+    using Pos = uint32_t;
+    static constexpr int kGroup = 4;
+    __device__ static E pack(int u, int v, int cx0, int cy0) {
+        return (E)((uint32_t)(uint16_t)(int16_t)(u - cx0) | ((uint32_t)(uint16_t)(int16_t)(v - cy0) << 16));
+    }
+    __device__ static int x(uint32_t e) { return (int)(int16_t)(e & 0xffffu); }
+    __device__ static int y(uint32_t e) { return (int)(int16_t)(e >> 16); }
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint32_t lanemask_le() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint32_t lanemask_ge() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_ge;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// A tile group: the threads that run one tile's pipeline. A CTA holds one group (single-image
+// launches) or several equal groups (batches of small configurations), each with its own
+// named barrier and its own partition of shared memory (everything after the kernel tables).
+struct Grp {
+    int tid, lane, warp;  // group-local indices
+    int nthreads;         // group size (the plan's CTA size)
+    int bar;              // named barrier; 0 is the whole CTA
+    int shift;            // byte shift of this group's shared-memory partition
+    __device__ __forceinline__ void sync() const {
+        if (bar == 0)
+            __syncthreads();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+    }
+};
+
+// Diagnostics: thread 0 records clock64() at phase boundaries when a buffer is attached.
+__device__ __forceinline__ void stamp(const Plan& P, int tile, int phase, const Grp& G) {
+    if (P.phase_clock != nullptr && G.tid == 0 && tile < P.phase_tiles)
+        P.phase_clock[tile * 8 + phase] = clock64();
+}
+
+__device__ __forceinline__ int span_lo(int s) { return (int)(int16_t)(s & 0xffff); }
+__device__ __forceinline__ int span_hi(int s) { return s >> 16; }
+
+// Region membership of one omnigram entry (Eq. 2); (px, py) is the window centre in the
+// entry's coordinate frame.
+template <int SHAPE, int W>
+struct Member;
+
+template <int W>
+struct Member<kShapeDisk, W> {
+    int r2;
+    __device__ __forceinline__ bool operator()(uint32_t e, int px, int py) const {
+        const int dx = Loc<W>::x(e) - px;
+        const int dy = Loc<W>::y(e) - py;
+        return dx * dx + dy * dy <= r2;   // Eq. 3 on the lattice
+    }
+};
+
+template <int W>
+struct Member<kShapeSpans, W> {
+    const int* spans;  // shared memory, per kernel row: lo | hi << 16
+    int ymin, nrows;
+    __device__ __forceinline__ bool operator()(uint32_t e, int px, int py) const {
+        const int i = Loc<W>::y(e) - py - ymin;
+        if ((unsigned)i >= (unsigned)nrows) return false;
+        const int s = spans[i];
+        const int dx = Loc<W>::x(e) - px;
+        return dx >= span_lo(s) && dx <= span_hi(s);
+    }
+};
+
+// Membership of the omnigram entries held in one 32-bit word, for a fixed window: bit k is
+// entry k of the word (two 16-bit entries, or one 32-bit entry).
+template <int SHAPE, int W>
+struct WordTest {
+    Member<SHAPE, W> m;
+    int px, py;
+    __device__ __forceinline__ void init(const Member<SHAPE, W>& mm, int x, int y) {
+        m = mm;
+        px = x;
+        py = y;
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t w) const {
+        if constexpr (W == 0)
+            return (uint32_t)m(w & 0xffffu, px, py) | ((uint32_t)m(w >> 16, px, py) << 1);
+        else
+            return (uint32_t)m(w, px, py);
+    }
+};
+
+// Disk with 8-bit coordinates: (x-px)^2 + (y-py)^2 <= r2 is evaluated as
+// x^2 + y^2 - 2(x px + y py) <= r2 - px^2 - py^2 with byte dot products on the packed pair.
+template <>
+struct WordTest<kShapeDisk, 0> {
+    int R;
+    int plo, phi;  // (px, py, 0, 0) and (0, 0, px, py) as signed bytes
+    __device__ __forceinline__ void init(const Member<kShapeDisk, 0>& mm, int px, int py) {
+        R = mm.r2 - px * px - py * py;
+        const uint32_t b = (uint32_t)(px & 0xff) | ((uint32_t)(py & 0xff) << 8);
+        plo = (int)b;
+        phi = (int)(b << 16);
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t w) const {
+        const int sq = __dp4a((int)w, (int)w, 0);
+        const int sq0 = __dp4a((int)(w & 0xffffu), (int)w, 0);
+        const int t0 = sq0 - 2 * __dp4a((int)w, plo, 0);
+        const int t1 = (sq - sq0) - 2 * __dp4a((int)w, phi, 0);
+        return (uint32_t)(t0 <= R) | ((uint32_t)(t1 <= R) << 1);
+    }
+};
+
+// Exact selection by ballot scans of the omnigram (Sec. 4.1, Sec. 4.2).
+// Given a pivot rank p and c = #{window members with rank < p}, returns the rank m of the
+// window element with window-rank `target`. All 32 lanes pass the same arguments and get
+// the same result; -1 means the counts were inconsistent (never expected).
+template <class E, class M>
+__device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, int p, int c, int target, int px,
+                                             int py, const M& member) {
+    const int lane = threadIdx.x & 31;
+    if (c <= target) {  // the answer is at or above p
+        int need = target - c + 1;
+        for (int v0 = p; v0 < N; v0 += 32) {
+            const int v = v0 + lane;
+            const bool in = v < N && member(om[v], px, py);
+            const uint32_t mask = __ballot_sync(kFull, in);
+            const int cnt = __popc(mask);
+            if (cnt >= need) {
+                const uint32_t hit = __ballot_sync(kFull, in && __popc(mask & lanemask_le()) == need);
+                return v0 + __ffs(hit) - 1;
+            }
+            need -= cnt;
+        }
+    } else {  // the answer is below p: walk down, the need-th member met is the answer
+        int need = c - target;
+        for (int v1 = p; v1 > 0; v1 -= 32) {
+            const int v = v1 - 32 + lane;
+            const bool in = v >= 0 && member(om[v], px, py);
+            const uint32_t mask = __ballot_sync(kFull, in);
+            const int cnt = __popc(mask);
+            if (cnt >= need) {
+                const uint32_t hit = __ballot_sync(kFull, in && __popc(mask & lanemask_ge()) == need);
+                return v1 - 32 + __ffs(hit) - 1;
+            }
+            need -= cnt;
+        }
+    }
+    return -1;
+}
+
+// Per-thread exact selection (vertical sweep): every lane refines its own window. It scans the
+// omnigram from its pivot in aligned groups of entries (one 128-bit load), counting members,
+// until the group holding the target-th member. While at least kHandoff lanes are still
+// scanning this is the cheapest schedule; the last few lanes of a warp (long jumps at edges and
+// impulses) are finished by warp-cooperative ballot scans instead of keeping 29+ lanes idle.
+// Same contract as ballot_select, per lane. All loops are bounded by the omnigram length.
+constexpr int kHandoff = 8;
+constexpr int kHandoffAfter = 12;  // groups
+
+template <int SHAPE, int W>
+__device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
+                                             int target, int px, int py, const Member<SHAPE, W>& member) {
+    constexpr int G = Loc<W>::kGroup;
+    constexpr uint32_t kAll = (1u << G) - 1;
+    const int lane = threadIdx.x & 31;
+    WordTest<SHAPE, W> wt;
+    wt.init(member, px, py);
+    const uint4* om128 = reinterpret_cast<const uint4*>(om);
+    const bool up = c <= target;
+    int need = up ? target - c + 1 : c - target;
+    int nextv = up ? p : p - 1;  // next omnigram entry to examine
+    const int glast = (N - 1) / G;
+    bool done = false;
+    int m = -1;
+    for (int it = 0; it <= glast + 1; ++it) {
+        // the hand-off test costs a vote, so it only starts once the typical scan is over
+        if (it >= kHandoffAfter && __popc(__ballot_sync(kFull, !done)) < kHandoff) break;
+        if (it < kHandoffAfter && !__any_sync(kFull, !done)) break;
+        if (!done) {
+            const int g = nextv >= 0 ? nextv / G : -1;
+            if (g < 0 || g > glast) {
+                done = true;
+            } else {
+                const uint4 q = om128[g];
+                constexpr int kb = G / 4;  // entries per word
+                uint32_t mask = wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb));
+                const int o = nextv - g * G;
+                mask &= up ? (kAll << o) & kAll : (kAll >> (G - 1 - o));
+                if (g == glast) mask &= kAll >> (G - 1 - (N - 1 - glast * G));
+                const int cnt = __popc(mask);
+                if (cnt >= need) {
+                    if (up) {
+                        for (int k = 1; k < need; ++k) mask &= mask - 1;  // drop the lowest need-1
+                        m = G * g + __ffs(mask) - 1;
+                    } else {
+                        for (int k = 1; k < need; ++k) mask ^= 1u << (31 - __clz(mask));  // drop the highest
+                        m = G * g + 31 - __clz(mask);
+                    }
+                    done = true;
+                } else {
+                    need -= cnt;
+                    nextv = up ? G * g + G : G * g - 1;
+                }
+            }
+        }
+    }
+    // hand-off: the remaining lanes, one window at a time, by ballot scans
+    uint32_t rest = __ballot_sync(kFull, !done);
+    while (rest) {
+        const int j = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const int upj = __shfl_sync(kFull, (int)up, j);
+        const int nj = __shfl_sync(kFull, nextv, j);
+        const int needj = __shfl_sync(kFull, need, j);
+        const int pxj = __shfl_sync(kFull, px, j);
+        const int pyj = __shfl_sync(kFull, py, j);
+        const int pj = upj ? nj : nj + 1;
+        const int cj = upj ? target + 1 - needj : target + needj;
+        const int mj = ballot_select(om, N, pj, cj, target, pxj, pyj, member);
+        if (lane == j) m = mj;
+    }
+    return m;
+}
+
+// Block-wide exclusive scan of 65536 16-bit counters packed two per word (bin 2k in the low
+// half of word k). Offsets stay below 2^16 because the footprint holds at most 65535 pixels.
+__device__ void scan_bins16(uint32_t* bins, uint32_t* wtot, const Plan& P, const Grp& G) {
+    const int lane = G.lane, warp = G.warp;
+    const int chunk = 32768 / P.nwarps;  // words per warp, a multiple of 128
+    uint4* b4 = reinterpret_cast<uint4*>(bins + warp * chunk);
+    uint32_t acc = 0;
+    for (int it = 0; it < chunk / 128; ++it) {
+        const uint4 q = b4[it * 32 + lane];
+        acc += ((q.x + (q.x >> 16)) & 0xffffu) + ((q.y + (q.y >> 16)) & 0xffffu) +
+               ((q.z + (q.z >> 16)) & 0xffffu) + ((q.w + (q.w >> 16)) & 0xffffu);
+    }
+    acc = __reduce_add_sync(kFull, acc);
+    if (lane == 0) wtot[warp] = acc;
+    G.sync();
+    if (warp == 0) {
+        const uint32_t x = lane < P.nwarps ? wtot[lane] : 0;
+        uint32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        wtot[lane] = incl - x;
+    }
+    G.sync();
+    uint32_t run = wtot[warp];
+    for (int it = 0; it < chunk / 128; ++it) {
+        uint4 q = b4[it * 32 + lane];
+        const uint32_t s = ((q.x + (q.x >> 16)) & 0xffffu) + ((q.y + (q.y >> 16)) & 0xffffu) +
+                           ((q.z + (q.z >> 16)) & 0xffffu) + ((q.w + (q.w >> 16)) & 0xffffu);
+        uint32_t incl = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t b = run + incl - s;
+        uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t lo = w[k] & 0xffffu, hi = w[k] >> 16;
+            w[k] = b | ((b + lo) << 16);
+            b += lo + hi;
+        }
+        b4[it * 32 + lane] = make_uint4(w[0], w[1], w[2], w[3]);
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    G.sync();
+}
+
+// The image as the tile pipeline reads it, held in registers.
+struct Img {
+    const char* in;
+    long long pitch;
+    int w, h;
+    __device__ __forceinline__ explicit Img(const Plan& P)
+        : in(static_cast<const char*>(P.in)), pitch(P.pitch), w(P.w), h(P.h) {}
+};
+
+template <int DT>
+__device__ __forceinline__ typename Traits<DT>::T load_px(const Img& im, int gx, int gy) {
+    using V = typename Traits<DT>::T;
+    const V* row = reinterpret_cast<const V*>(im.in + (long long)clampi(gy, 0, im.h - 1) * im.pitch);
+    return __ldg(row + clampi(gx, 0, im.w - 1));
+}
+
+// Counting-sort ordinal transform for 8/16-bit data (Sec. 4.1, Eq. 5): histogram of the
+// footprint, exclusive prefix, then every pixel takes the next free ordinal of its value.
+// Ties get consecutive ordinals in arrival order, which is all the method needs.
+template <int DT, int W>
+__device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t* bins, uint32_t* misc,
+                                        typename Loc<W>::E* om, int gx0, int gy0, const Grp& G) {
+    const int tid = G.tid, lane = G.lane, warp = G.warp;
+    const Img im(P);
+    const int SH = P.SH, nwarps = P.nwarps, cx0 = P.cx0, cy0 = P.cy0;
+    constexpr bool k16 = DT == FIM_U16;
+    const int nwords = k16 ? 32768 : 256;
+    for (int i = tid * 4; i < nwords; i += P.threads * 4)
+        *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
+    G.sync();
+    for (int v = warp; v < SH; v += nwarps) {
+        const int fr = frow[v];
+        for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
+            const uint32_t key = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
+            if (k16)
+                atomicAdd(&bins[key >> 1], 1u << ((key & 1u) << 4));
+            else
+                atomicAdd(&bins[key], 1u);
+        }
+    }
+    G.sync();
+    if (k16) {
+        scan_bins16(bins, misc, P, G);
+    } else {
+        if (warp == 0) {
+            uint32_t c[8], s = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                c[k] = bins[lane * 8 + k];
+                s += c[k];
+            }
+            uint32_t incl = s;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t b = incl - s;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                bins[lane * 8 + k] = b;
+                b += c[k];
+            }
+        }
+        G.sync();
+    }
+    for (int v = warp; v < SH; v += nwarps) {
+        const int fr = frow[v];
+        for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
+            const uint32_t key = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
+            uint32_t o;
+            if (k16) {
+                const uint32_t sh = (key & 1u) << 4;
+                o = (atomicAdd(&bins[key >> 1], 1u << sh) >> sh) & 0xffffu;
+            } else {
+                o = atomicAdd(&bins[key], 1u);
+            }
+            om[o] = Loc<W>::pack(u, v, cx0, cy0);
+        }
+    }
+}
+
+// Stable LSD radix ordinal transform: 8-bit passes over bounding-box positions, four for
+// 32-bit float keys, two for 16-bit data. Each warp owns one contiguous segment of the current order; a
+// pixel's new place is its (digit, warp)-major exclusive offset plus its position among
+// equal digits earlier in the segment (warp match). Histograms are laid out warp-major with
+// a pad word so that the leaders of one warp never share a bank. The sorted positions end in
+// list B, which is then rewritten in place as the omnigram.
+template <int DT, int W>
+__device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t* keys, typename Loc<W>::Pos* bufA,
+                                        typename Loc<W>::Pos* bufB, uint32_t* hist, uint32_t* wsum, int gx0, int gy0,
+                                        const Grp& G) {
+    using Pos = typename Loc<W>::Pos;
+    const int tid = G.tid, lane = G.lane, warp = G.warp;
+    const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
+    constexpr int HS = kSortBins + 1;
+    const Img im(P);
+    for (int v = warp; v < P.SH; v += nwarps) {
+        const int fr = frow[v];
+        for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32)
+            keys[v * S + u] = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
+    }
+    G.sync();
+    const int area = S * P.SH;
+    const Pos* src = nullptr;
+    Pos* dst = bufA;
+    constexpr int kPasses = DT == FIM_F32 ? 4 : 2;  // 8-bit digits of 32- or 16-bit keys
+    static_assert(kPasses % 2 == 0, "the sorted positions must end in list B");
+    for (int pass = 0; pass < kPasses; ++pass) {
+        const int shift = 8 * pass;
+        const int len = pass == 0 ? area : P.N;
+        const int seg = ((len + nwarps - 1) / nwarps + 31) & ~31;
+        const int s0 = min(len, warp * seg), s1 = min(len, s0 + seg);
+        uint32_t* hw = hist + warp * HS;
+        for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
+        __syncwarp();
+        for (int b = s0; b < s1; b += 32) {
+            const int i = b + lane;
+            bool valid = i < s1;
+            int pos = 0;
+            if (valid) {
+                if (pass == 0) {
+                    const int v = (int)__umulhi((unsigned)i, P.div_magic);
+                    const int u = i - v * S;
+                    const int fr = frow[v];
+                    valid = u >= span_lo(fr) && u <= span_hi(fr);
+                    pos = i;
+                } else {
+                    pos = (int)src[i];
+                }
+            }
+            const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
+            const uint32_t peers = __match_any_sync(kFull, d);
+            if (valid && lane == __ffs(peers) - 1) hw[d] += __popc(peers);
+            __syncwarp();
+        }
+        G.sync();
+        {   // exclusive scan in (digit, warp) order: each thread takes 8 consecutive counters
+            const int e0 = tid * 8;  // 256 * nwarps counters over 32 * nwarps threads
+            uint32_t c[8];
+            uint32_t local = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int e = e0 + j, d = e / nwarps, wq = e - d * nwarps;
+                c[j] = hist[wq * HS + d];
+                local += c[j];
+            }
+            uint32_t incl = local;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) wsum[warp] = incl;
+            G.sync();
+            if (warp == 0) {
+                const uint32_t x = lane < nwarps ? wsum[lane] : 0;
+                uint32_t y = x;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, y, o);
+                    if (lane >= o) y += t;
+                }
+                wsum[lane] = y - x;
+            }
+            G.sync();
+            uint32_t run = incl - local + wsum[warp];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int e = e0 + j, d = e / nwarps, wq = e - d * nwarps;
+                hist[wq * HS + d] = run;
+                run += c[j];
+            }
+        }
+        G.sync();
+        for (int b = s0; b < s1; b += 32) {
+            const int i = b + lane;
+            bool valid = i < s1;
+            int pos = 0;
+            if (valid) {
+                if (pass == 0) {
+                    const int v = (int)__umulhi((unsigned)i, P.div_magic);
+                    const int u = i - v * S;
+                    const int fr = frow[v];
+                    valid = u >= span_lo(fr) && u <= span_hi(fr);
+                    pos = i;
+                } else {
+                    pos = (int)src[i];
+                }
+            }
+            const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
+            const uint32_t peers = __match_any_sync(kFull, d);
+            uint32_t base = 0;
+            if (valid) base = hw[d];
+            __syncwarp();
+            if (valid) {
+                dst[base + __popc(peers & lanemask_lt())] = (Pos)pos;
+                if (lane == __ffs(peers) - 1) hw[d] = base + __popc(peers);
+            }
+            __syncwarp();
+        }
+        G.sync();
+        src = dst;
+        dst = (dst == bufA) ? bufB : bufA;
+    }
+    // an even number of passes: the sorted positions are in B; rewrite them in place as entries
+    typename Loc<W>::E* om = reinterpret_cast<typename Loc<W>::E*>(bufB);
+    for (int v = tid; v < P.N; v += nthreads) {
+        const int pos = (int)bufB[v];
+        const int y = (int)__umulhi((unsigned)pos, P.div_magic);
+        om[v] = Loc<W>::pack(pos - y * S, y, P.cx0, P.cy0);
+    }
+}
+
+// ---- learned rank bracket (seed windows) ---------------------------------------------------
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// Features of the seed window centred at box position (cu, cv): the tile's normalised value
+// quantiles (already in q[0..31]) and the ranks / N of the 3x3 pixels around the centre
+// (the centre's own rank where a neighbour lies outside the footprint).
+__device__ __forceinline__ void seed_features(const uint16_t* ord, int SP, const int* frow, int SH, int N, int cu,
+                                              int cv, const float* q, float* fa, float* fb) {
+    const int lane = threadIdx.x & 31;
+    *fa = q[lane];
+    float nb = 0.f;
+    if (lane < kNeigh) {
+        int u = cu + lane % 3 - 1, v = cv + lane / 3 - 1;
+        bool in = v >= 0 && v < SH;
+        if (in) {
+            const int fr = frow[v];
+            in = u >= span_lo(fr) && u <= span_hi(fr);
+        }
+        if (!in) {
+            u = cu;
+            v = cv;
+        }
+        nb = (float)ord[v * SP + u] / (float)N;
+    }
+    *fb = nb;
+}
+
+// Visits the ranks of every pixel of a window (row i of the kernel at ctr + (ymin + i) * SP,
+// ctr being the window centre's ordinal-image position shifted by ymin rows). Lane l takes
+// kernel rows l, l+32, ... and walks each from a lane-dependent column, so the 32 pixels
+// visited at once lie far apart (their ranks rarely share a histogram bin). Four ranks are
+// loaded before they are handed to `f`, so the loads of a group overlap instead of each
+// waiting behind the previous group's shared-memory atomics.
+template <class Fn>
+__device__ __forceinline__ void window_walk(const int* spans, int nrows, const uint16_t* ctr, int SP, Fn&& f) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < nrows; i += 32) {
+        const int sp = spans[i];
+        const int width = span_hi(sp) - span_lo(sp) + 1;
+        const uint16_t* row = ctr + i * SP + span_lo(sp);
+        int x = (lane * 37) % width;
+        int k = 0;
+        for (; k + 4 <= width; k += 4) {
+            int x1 = x + 1, x2 = x + 2, x3 = x + 3;
+            if (x1 >= width) x1 -= width;
+            if (x2 >= width) x2 -= width;
+            if (x3 >= width) x3 -= width;
+            const int r0 = row[x], r1 = row[x1], r2 = row[x2], r3 = row[x3];
+            f(r0);
+            f(r1);
+            f(r2);
+            f(r3);
+            x = x3 + 1 == width ? 0 : x3 + 1;
+        }
+        for (; k < width; ++k) {
+            f((int)row[x]);
+            x = (x + 1 == width) ? 0 : x + 1;
+        }
+    }
+}
+
+// Seed histogram (kSeedBins bins of one warp): the bin holding window-rank `target` when// Seed histogram (kSeedBins bins of one warp): the bin holding window-rank `target` when
+// `base` window members lie below bin 0. Returns the bin and, in *below, the members below it.
+__device__ __forceinline__ int hist_pick(const uint32_t* hw, int base, int target, int* below) {
+    const int lane = threadIdx.x & 31;
+    constexpr int per = kSeedBins / 32;
+    uint32_t local = 0;
+    for (int j = 0; j < per; ++j) local += hw[lane * per + j];
+    uint32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t tt = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += tt;
+    }
+    const int excl = base + (int)(incl - local);
+    const bool mine = excl <= target && target < base + (int)incl;
+    const uint32_t who = __ballot_sync(kFull, mine);
+    int bin = 0, run = 0;
+    if (mine) {
+        run = excl;
+        int j = 0;
+        for (; j < per - 1; ++j) {
+            const int c = (int)hw[lane * per + j];
+            if (run + c > target) break;
+            run += c;
+        }
+        bin = lane * per + j;
+    }
+    const int src = who ? __ffs(who) - 1 : 0;
+    *below = __shfl_sync(kFull, run, src);
+    return __shfl_sync(kFull, bin, src);
+}
+
+template <class T>
+__device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, int loc) {
+    return reinterpret_cast<T*>(loc >= 0 ? smem + loc : gslice + (-(long long)loc - 1));
+}
+
+template <int DT, int SHAPE, int W, int OG>
+__device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G) {
+    extern __shared__ __align__(16) unsigned char smem_base[];
+    unsigned char* const smem = smem_base + G.shift;  // this group's partition (tables excluded)
+    using V = typename Traits<DT>::T;
+    using E = typename Loc<W>::E;
+    const int tid = G.tid;
+    const int lane = G.lane;
+    const int warp = G.warp;
+    const int nthreads = P.threads;
+    const int nwarps = P.nwarps;
+    const int SP = P.SP, N = P.N, TX = P.Tx, TY = P.Ty;
+    const int tx0 = (tile % P.tiles_x) * TX;
+    const int ty0 = (tile / P.tiles_x) * TY;
+    const int gx0 = tx0 + P.xmin;  // global coordinates of bounding-box pixel (0, 0)
+    const int gy0 = ty0 + P.ymin;
+    const int cx0 = P.cx0, cy0 = P.cy0, xmin = P.xmin, ymin = P.ymin, hist_shift = P.hist_shift;
+
+    const int2* vtab = reinterpret_cast<const int2*>(smem_base + P.off_vtab);
+    const int2* htab = reinterpret_cast<const int2*>(smem_base + P.off_htab);
+    const int* spans = reinterpret_cast<const int*>(smem_base + P.off_spans);
+    const int* frow = reinterpret_cast<const int*>(smem_base + P.off_frow);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(smem + P.off_misc);
+    // The omnigram's home is fixed per instantiation (OG), so the compiler keeps shared-memory
+    // accesses as such; everything else of the solve always lives in shared memory.
+    E* om = OG ? reinterpret_cast<E*>(gslice + (-(long long)P.loc_om - 1)) : reinterpret_cast<E*>(smem + P.loc_om);
+    uint16_t* ord = reinterpret_cast<uint16_t*>(smem + P.loc_ord);
+    uint16_t* med = reinterpret_cast<uint16_t*>(smem + P.loc_med);
+    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + P.loc_shist);
+
+    // ---- 1. ordinal transform ------------------------------------------------------------------
+    stamp(P, tile, 1, G);
+    // float data always takes the radix sort; 16-bit data takes it in small CTAs, where the
+    // counting sort's 65536 bins would keep other CTAs off the SM
+    if (DT == FIM_F32 || (DT == FIM_U16 && P.sort == kSortRadix))
+        ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
+                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
+                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
+                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, gx0, gy0, G);
+    else if constexpr (DT != FIM_F32)
+        ordinal_transform_count<DT, W>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), misc, om, gx0, gy0,
+                                       G);
+    G.sync();
+
+    // ---- 2. ordinal image I (Eq. 4) ------------------------------------------------------------
+    stamp(P, tile, 2, G);
+    for (int v = tid; v < N; v += nthreads) {
+        const uint32_t e = om[v];
+        ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)v;
+    }
+    G.sync();
+
+    Member<SHAPE, W> member;
+    if constexpr (SHAPE == kShapeDisk) {
+        member.r2 = P.r2;
+    } else {
+        member.spans = spans;
+        member.ymin = P.ymin;
+        member.nrows = P.nrows;
+    }
+    const int target = P.rank;
+    const int BH = TY / P.RB;      // band height
+    const int GW = TX / P.G;       // seed spacing within a seed row
+    // feasible median ranks of any window of this tile (Fig. 10): [lof, hif]
+    const int lof = target, hif = N - P.n + target;
+
+    // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
+    // (or, with a learned bracket, two exact counts at predicted ranks, then ballot refine)
+    stamp(P, tile, 3, G);
+    const bool learned = P.model != nullptr;
+    float* quant = reinterpret_cast<float*>(misc);  // the sort's scan scratch is free from here on
+    if (learned || P.samples != nullptr) {
+        if (warp == 0) {  // normalised value quantiles of the footprint: C at N (j + 1/2) / 32
+            const int q = min(N - 1, (int)(((long long)N * (2 * lane + 1)) / (2 * kQuantiles)));
+            const uint32_t e = om[q];
+            const float v = (float)load_px<DT>(Img(P), gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
+            const float mid = __shfl_sync(kFull, v, kQuantiles / 2);
+            const float spread = __shfl_sync(kFull, v, 7 * kQuantiles / 8) - __shfl_sync(kFull, v, kQuantiles / 8);
+            const float z = (v - mid) / (spread > 0.f ? spread : 1.f);
+            quant[lane] = fminf(fmaxf(z, -8.f), 8.f);
+        }
+        G.sync();
+    }
+    const int nseeds = P.RB * P.G;
+    static_assert(kHidden + kNeigh + 2 * kHidden <= kSeedBins, "MLP activations fit a seed histogram per seed");
+    if (learned) {
+        // Learned bracket (extension): the bracket MLP runs block-wide over a chunk of seeds
+        // (thread per (seed, hidden unit), activations in the seed-histogram buffers), then one
+        // warp per seed counts its window at the bracket ends, histograms the ranks inside the
+        // bracket finely, and scans Omega from the fine bin of the target (or, on a miss, from
+        // the bracket end the target lies beyond).
+        const uint16_t* wts =
+            P.off_model >= 0 ? reinterpret_cast<const uint16_t*>(smem_base + P.off_model) : P.model;
+        const int chunk_max = min(nwarps, nseeds);
+        // activations: 64 + chunk * (9 + 64 + 64) floats, within the chunk * 1 KiB of histograms
+        float* hbase = reinterpret_cast<float*>(shist);  // layer-1 pre-activation of the quantiles
+        float* xs = hbase + kHidden;                      // [chunk][kNeigh]
+        float* h1 = xs + chunk_max * kNeigh;              // [chunk][kHidden]
+        float* h2 = h1 + chunk_max * kHidden;             // [chunk][kHidden]
+        for (int j = tid; j < kHidden; j += nthreads) {
+            float h = bf16_to_f32(wts[kOffB1 + j]);
+            for (int i = 0; i < kQuantiles; ++i) h = fmaf(quant[i], bf16_to_f32(wts[kOffW1 + i * kHidden + j]), h);
+            hbase[j] = h;
+        }
+        for (int c0 = 0; c0 < nseeds; c0 += chunk_max) {
+            const int chunk = min(chunk_max, nseeds - c0);
+            if (warp < chunk) {
+                const int sd = c0 + warp;
+                const int band = sd / P.G, g = sd % P.G;
+                const int cu = g * GW + GW / 2 - xmin, cv = band * BH + BH / 2 - ymin;
+                float fa, fb;
+                seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+                if (lane < kNeigh) xs[warp * kNeigh + lane] = fb;
+            }
+            G.sync();
+            for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
+                const int sl = idx / kHidden, j = idx % kHidden;
+                float h = hbase[j];
+#pragma unroll
+                for (int i = 0; i < kNeigh; ++i)
+                    h = fmaf(xs[sl * kNeigh + i], bf16_to_f32(wts[kOffW1 + (kQuantiles + i) * kHidden + j]), h);
+                h1[idx] = fmaxf(h, 0.f);
+            }
+            G.sync();
+            for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
+                const int sl = idx / kHidden, j = idx % kHidden;
+                float h = bf16_to_f32(wts[kOffB2 + j]);
+#pragma unroll 8
+                for (int k = 0; k < kHidden; ++k) h = fmaf(h1[sl * kHidden + k], bf16_to_f32(wts[kOffW2 + k * kHidden + j]), h);
+                h2[idx] = fmaxf(h, 0.f);
+            }
+            G.sync();
+            int lo = 0, hi = 0;
+            if (warp < chunk) {  // output layer: lanes hold hidden units lane and lane + 32
+                const float x0 = h2[warp * kHidden + lane], x1 = h2[warp * kHidden + lane + 32];
+                float o0 = bf16_to_f32(wts[kOffW3 + lane * 2]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2]) * x1;
+                float o1 = bf16_to_f32(wts[kOffW3 + lane * 2 + 1]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2 + 1]) * x1;
+                for (int o = 16; o > 0; o >>= 1) {
+                    o0 += __shfl_xor_sync(kFull, o0, o);
+                    o1 += __shfl_xor_sync(kFull, o1, o);
+                }
+                o0 += bf16_to_f32(wts[kOffB3]);
+                o1 += bf16_to_f32(wts[kOffB3 + 1]);
+                const float sig = __expf(fminf(fmaxf(o1, -8.f), 2.f)) * P.bracket_z;
+                const float span = (float)(hif - lof);
+                lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
+                hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
+            }
+            G.sync();  // the histograms below overwrite the activations
+            if (warp < chunk) {
+                const int sd = c0 + warp;
+                const int band = sd / P.G, g = sd % P.G;
+                const int s = g * GW + GW / 2, t = band * BH + BH / 2;
+                const int cu = s - xmin, cv = t - ymin;
+                // One pass counts the window below lo and at or below hi and histograms the ranks
+                // inside [lo, hi] in kFineBins fine bins. Every pixel makes one atomic: pixels
+                // outside the bracket add to a lane-private spare word (its own bank), so the
+                // bracket's few pixels are the only ones that can collide.
+                constexpr int kFineBins = kSeedBins - 32;
+                int hb = 0;
+                while (((hi - lo) >> hb) >= kFineBins) ++hb;
+                uint32_t* hw = shist + warp * kSeedBins;
+                for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+                __syncwarp();
+                int clo = 0, chi = 0;
+                window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
+                    clo += r < lo;
+                    chi += r <= hi;
+                    const bool in = (unsigned)(r - lo) <= (unsigned)(hi - lo);
+                    atomicAdd(&hw[in ? (r - lo) >> hb : kFineBins + lane], 1u);
+                });
+                clo = __reduce_add_sync(kFull, clo);
+                chi = __reduce_add_sync(kFull, chi);
+                __syncwarp();
+                int pivot, below, kind;
+                if (target < clo) {         // below the bracket: walk down from lo
+                    pivot = lo;
+                    below = clo;
+                    kind = 2;
+                } else if (target >= chi) { // above the bracket: walk up from hi + 1
+                    pivot = hi + 1;
+                    below = chi;
+                    kind = 3;
+                } else {                    // inside: the fine bin holding the target (the spare
+                    kind = 1;               // words come after every fine bin, so are not reached)
+                    pivot = lo + (hist_pick(hw, clo, target, &below) << hb);
+                }
+                const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+                if (m < 0) set_status(FIM_ERR_INTERNAL);
+                if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+                if (P.stats != nullptr && lane == 0) {
+                    atomicAdd(P.stats + 0, 1ull);
+                    atomicAdd(P.stats + kind, 1ull);
+                    atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
+                }
+            }
+            G.sync();  // the next chunk reuses the activation buffers
+        }
+    } else {
+        for (int sd = warp; sd < nseeds; sd += nwarps) {
+            const int band = sd / P.G, g = sd % P.G;
+            const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
+            const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
+            float fa = 0.f, fb = 0.f;
+            if (P.samples != nullptr) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+            // one histogram per concurrently solved seed
+            uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
+            for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+            __syncwarp();
+            window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
+                        [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
+            __syncwarp();
+            int below = 0;
+            const int pivot = hist_pick(hw, 0, target, &below) << hist_shift;
+            const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+            if (m < 0) set_status(FIM_ERR_INTERNAL);
+            if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+            if (P.samples != nullptr) {  // training row: features and the exact median's place in [lof, hif]
+                unsigned int row = 0;
+                if (lane == 0) row = atomicAdd(P.sample_count, 1u);
+                row = __shfl_sync(kFull, row, 0);
+                if ((int)row < P.sample_cap) {
+                    float* dst = P.samples + (size_t)row * (kFeatures + 1);
+                    dst[lane] = fa;
+                    if (lane < kNeigh) dst[kQuantiles + lane] = fb;
+                    if (lane == 0) dst[kFeatures] = hif > lof ? (float)(max(m, 0) - lof) / (float)(hif - lof) : 0.5f;
+                }
+            }
+            if (P.stats != nullptr && lane == 0) {
+                atomicAdd(P.stats + 0, 1ull);
+                atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
+            }
+            __syncwarp();
+        }
+    }
+    G.sync();
+
+    // ---- 4. seed rows: horizontal slides, lanes split the kernel rows ----------------------
+    stamp(P, tile, 4, G);
+    for (int job = warp; job < 2 * P.RB * P.G; job += nwarps) {
+        const int sd = job >> 1, right = job & 1;
+        const int band = sd / P.G, g = sd % P.G;
+        int s = g * GW + GW / 2;
+        const int t = band * BH + BH / 2;
+        const int steps = right ? (GW - GW / 2 - 1) : (GW / 2);
+        int cu = s - xmin;
+        const int cv = t - ymin;
+        int p = med[t * TX + s];
+        constexpr int kRowsPerLane = (kMaxExtent + 31) / 32;
+        int eo[kRowsPerLane], lo[kRowsPerLane];  // this lane's rows: entering / leaving offsets
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) {
+            const int i = lane + 32 * q;
+            eo[q] = lo[q] = 0;  // rows beyond the kernel compare the centre with itself: no change
+            if (i < P.nrows) {
+                const int2 o = htab[i];
+                eo[q] = right ? o.y : o.x - 1;
+                lo[q] = right ? o.x : o.y - 1;
+            }
+        }
+        for (int k = 0; k < steps; ++k) {
+            const uint16_t* ctr = ord + cv * SP + cu;
+            int d = 0;
+#pragma unroll
+            for (int q = 0; q < kRowsPerLane; ++q)
+                if (32 * q < P.nrows) d += (int)(ctr[eo[q]] < p) - (int)(ctr[lo[q]] < p);
+            d = __reduce_add_sync(kFull, d);
+            cu += right ? 1 : -1;
+            s += right ? 1 : -1;
+            const int m = ballot_select(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
+            if (m < 0) set_status(FIM_ERR_INTERNAL);
+            p = max(m, 0);
+            if (lane == 0) med[t * TX + s] = (uint16_t)p;
+        }
+    }
+    G.sync();
+
+    // ---- 5. vertical sweeps: thread per window column, per-thread refinement ----------------
+    stamp(P, tile, 5, G);
+    if (warp < P.vthreads / 32) {
+        const int groups = TX / 32;
+        const int cg = warp % groups;
+        const int rest = warp / groups;
+        const int band = P.vmix ? (rest + lane) % P.RB : rest % P.RB;  // per lane with mixing
+        const int down = rest / P.RB;  // 0: up, 1: down
+        const int s = cg * 32 + lane;
+        int t = band * BH + BH / 2;
+        const int steps = down ? (BH - BH / 2 - 1) : (BH / 2);
+        const int cu = s - xmin;
+        int cv = t - ymin;
+        int p = med[t * TX + s];
+        const int ncols = P.ncols;
+        const int eoff = down ? 0 : -SP;
+        for (int k = 0; k < steps; ++k) {
+            const uint16_t* ctr = ord + cv * SP + cu + eoff;
+            int d = 0;
+            if (down) {
+#pragma unroll 4
+                for (int j = 0; j < ncols; ++j) {
+                    const int2 o = vtab[j];
+                    d += (int)(ctr[o.y] < p) - (int)(ctr[o.x] < p);
+                }
+            } else {
+#pragma unroll 4
+                for (int j = 0; j < ncols; ++j) {
+                    const int2 o = vtab[j];
+                    d += (int)(ctr[o.x] < p) - (int)(ctr[o.y] < p);
+                }
+            }
+            cv += down ? 1 : -1;
+            t += down ? 1 : -1;
+            const int mine = thread_select<SHAPE, W>(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
+            if (mine < 0) set_status(FIM_ERR_INTERNAL);
+            p = max(mine, 0);
+            med[t * TX + s] = (uint16_t)p;
+        }
+    }
+    G.sync();
+
+    // ---- 6. output: the input value at Omega[m] ------------------------------------------------
+    stamp(P, tile, 6, G);
+    const Img im(P);
+    char* out = static_cast<char*>(P.out);
+    const int txshift = P.txshift;
+    for (int idx = tid; idx < TX * TY; idx += nthreads) {
+        const int t = idx >> txshift, s = idx & (TX - 1);
+        const int gx = tx0 + s, gy = ty0 + t;
+        if (gx >= im.w || gy >= im.h) continue;
+        const uint32_t e = om[med[idx]];
+        const V val = load_px<DT>(im, gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
+        reinterpret_cast<V*>(out + (long long)gy * im.pitch)[gx] = val;
+    }
+    G.sync();
+    stamp(P, tile, 7, G);
+}
+
+__device__ __forceinline__ void load_tables(const Plan& P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int2* vtab = reinterpret_cast<int2*>(smem + P.off_vtab);
+    int2* htab = reinterpret_cast<int2*>(smem + P.off_htab);
+    int* spans = reinterpret_cast<int*>(smem + P.off_spans);
+    int* frow = reinterpret_cast<int*>(smem + P.off_frow);
+    for (int i = tid; i < P.ncols; i += nt) vtab[i] = make_int2(P.vtab[2 * i], P.vtab[2 * i + 1]);
+    for (int i = tid; i < P.nrows; i += nt) {
+        htab[i] = make_int2(P.htab[2 * i], P.htab[2 * i + 1]);
+        spans[i] = P.spans[i];
+    }
+    for (int i = tid; i < P.SH; i += nt) frow[i] = P.frow[i];
+    if (P.off_model >= 0 && P.model != nullptr) {  // kMlpParams is even: copy 32-bit pairs
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(P.model);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(smem + P.off_model);
+        for (int i = tid; i < kMlpParams / 2; i += nt) dst[i] = src[i];
+    }
+}
+
+}  // namespace
+}  // namespace fim
