@@ -208,7 +208,7 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->S = ts.Tx + (k->xmax - k->xmin);
     p->SH = ts.Ty + (k->ymax - k->ymin);
     if (p->S > kMaxSide || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
-    p->wide = (p->S > 256 || p->SH > 256) ? 1 : 0;
+    p->wide = (p->S > 255 || p->SH > 255) ? 1 : 0;  // 8-bit coordinates keep -128 free
     p->SP = (p->S + 1) & ~1;
     if ((p->SP / 2) % 2 == 0) p->SP += 2;  // odd number of 32-bit words per row: no bank aliasing
     p->tiles_x = (w + ts.Tx - 1) / ts.Tx;

@@ -24,7 +24,7 @@
 // below the pivot is exactly the target rank, and a slide only adds the change.
 //
 // W selects the omnigram encoding: W = 0 packs a location as two int8 coordinates (footprint
-// box up to 256 x 256, Sec. 4.1); W = 1 uses two int16 coordinates for larger boxes. OG = 1
+// box up to 255 x 255, Sec. 4.1; -128 marks padding); W = 1 uses two int16 coordinates. OG = 1
 // keeps the omnigram in the CTA's global scratch slice when shared memory cannot hold it.
 #include <stdint.h>
 
@@ -72,6 +72,7 @@ struct Loc<0> {
     using E = uint16_t;    // entry
     using Pos = uint16_t;  // bounding-box position in the radix lists
     static constexpr int kGroup = 8;  // entries per 128-bit load
+    static constexpr E kSentinel = 0x8080;  // (-128, -128): outside every window of a box < 256
     __device__ static E pack(int u, int v, int cx0, int cy0) {
         return (E)((uint32_t)(uint8_t)(int8_t)(u - cx0) | ((uint32_t)(uint8_t)(int8_t)(v - cy0) << 8));
     }
@@ -83,6 +84,7 @@ struct Loc<1> {
     using E = uint32_t;
     using Pos = uint32_t;
     static constexpr int kGroup = 4;
+    static constexpr E kSentinel = 0xC000C000u;  // (-16384, -16384): far outside every window
     __device__ static E pack(int u, int v, int cx0, int cy0) {
         return (E)((uint32_t)(uint16_t)(int16_t)(u - cx0) | ((uint32_t)(uint16_t)(int16_t)(v - cy0) << 16));
     }
@@ -265,21 +267,24 @@ __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restric
     const int glast = (N - 1) / G;
     bool done = false;
     int m = -1;
+    // Entries past N up to the last group's end are sentinels that are never members, so only
+    // the first group needs a mask: the entries on the far side of the pivot.
+    const int o0 = nextv & (G - 1);
+    uint32_t first = up ? (kAll << o0) & kAll : kAll >> (G - 1 - o0);
+    constexpr int kShift = G == 8 ? 3 : 2;
     for (int it = 0; it <= glast + 1; ++it) {
         // the hand-off test costs a vote, so it only starts once the typical scan is over
         if (it >= kHandoffAfter && __popc(__ballot_sync(kFull, !done)) < kHandoff) break;
         if (it < kHandoffAfter && !__any_sync(kFull, !done)) break;
         if (!done) {
-            const int g = nextv >= 0 ? nextv / G : -1;
-            if (g < 0 || g > glast) {
+            const int g = nextv >> kShift;  // -1 below entry 0
+            if ((unsigned)g > (unsigned)glast) {
                 done = true;
             } else {
                 const uint4 q = om128[g];
                 constexpr int kb = G / 4;  // entries per word
-                uint32_t mask = wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb));
-                const int o = nextv - g * G;
-                mask &= up ? (kAll << o) & kAll : (kAll >> (G - 1 - o));
-                if (g == glast) mask &= kAll >> (G - 1 - (N - 1 - glast * G));
+                uint32_t mask = (wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb))) & first;
+                first = kAll;
                 const int cnt = __popc(mask);
                 if (cnt >= need) {
                     if (up) {
@@ -445,10 +450,12 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
     }
 }
 
-// Stable LSD radix ordinal transform: 8-bit passes over bounding-box positions, four for
-// 32-bit float keys, two for 16-bit data. Each warp owns one contiguous segment of the current order; a
-// pixel's new place is its (digit, warp)-major exclusive offset plus its position among
-// equal digits earlier in the segment (warp match). Histograms are laid out warp-major with
+// LSD radix ordinal transform: 8-bit passes over bounding-box positions, four for 32-bit
+// float keys, two for 16-bit data. Every pass after the first is stable; the first may order
+// equal digits arbitrarily (shared-memory atomics), since the later passes keep that order.
+// Each warp owns one contiguous segment of the current order; in a stable pass a pixel's new
+// place is its (digit, warp)-major exclusive offset plus its position among equal digits
+// earlier in the segment (warp match). Histograms are laid out warp-major with
 // a pad word so that the leaders of one warp never share a bank. The sorted positions end in
 // list B, which is then rewritten in place as the omnigram.
 template <int DT, int W>
@@ -495,9 +502,13 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
                 }
             }
             const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
-            const uint32_t peers = __match_any_sync(kFull, d);
-            if (valid && lane == __ffs(peers) - 1) hw[d] += __popc(peers);
-            __syncwarp();
+            if (pass == 0) {  // the first pass need not be stable: plain shared-memory counts
+                if (valid) atomicAdd(&hw[d], 1u);
+            } else {
+                const uint32_t peers = __match_any_sync(kFull, d);
+                if (valid && lane == __ffs(peers) - 1) hw[d] += __popc(peers);
+                __syncwarp();
+            }
         }
         G.sync();
         {   // exclusive scan in (digit, warp) order: each thread takes 8 consecutive counters
@@ -552,6 +563,10 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
                 }
             }
             const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
+            if (pass == 0) {  // equal digits may land in any order: the next passes are stable
+                if (valid) dst[atomicAdd(&hw[d], 1u)] = (Pos)pos;
+                continue;
+            }
             const uint32_t peers = __match_any_sync(kFull, d);
             uint32_t base = 0;
             if (valid) base = hw[d];
@@ -722,6 +737,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     for (int v = tid; v < N; v += nthreads) {
         const uint32_t e = om[v];
         ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)v;
+    }
+    {   // pad the last 128-bit group with sentinels no window contains
+        const int pad = ((N + Loc<W>::kGroup - 1) & ~(Loc<W>::kGroup - 1)) - N;
+        if (tid < pad) om[N + tid] = Loc<W>::kSentinel;
     }
     G.sync();
 
