@@ -467,106 +467,108 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
     constexpr int HS = kSortBins + 1;
     const Img im(P);
-    for (int v = warp; v < P.SH; v += nwarps) {
+    const int area = S * P.SH;
+    uint32_t* hw = hist + warp * HS;
+    // Exclusive scan of the per-warp digit counts in (digit, warp) order, in place: each thread
+    // takes 8 consecutive counters (256 * nwarps counters over 32 * nwarps threads).
+    auto scan_counts = [&]() {
+        const int e0 = tid * 8;
+        uint32_t c[8];
+        uint32_t local = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = e0 + j, d = e / nwarps, wq = e - d * nwarps;
+            c[j] = hist[wq * HS + d];
+            local += c[j];
+        }
+        uint32_t incl = local;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        G.sync();
+        if (warp == 0) {
+            const uint32_t x = lane < nwarps ? wsum[lane] : 0;
+            uint32_t y = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, y, o);
+                if (lane >= o) y += t;
+            }
+            wsum[lane] = y - x;
+        }
+        G.sync();
+        uint32_t run = incl - local + wsum[warp];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = e0 + j, d = e / nwarps, wq = e - d * nwarps;
+            hist[wq * HS + d] = run;
+            run += c[j];
+        }
+    };
+    // box position i lies in the footprint (Fig. 10)
+    auto inside = [&](int i) {
+        const int v = (int)__umulhi((unsigned)i, P.div_magic);
         const int fr = frow[v];
-        for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32)
-            keys[v * S + u] = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
+        const int u = i - v * S;
+        return u >= span_lo(fr) && u <= span_hi(fr);
+    };
+    // Pass 0, fused with the footprint load: every thread takes box positions tid, tid +
+    // nthreads, ... (coalesced rows), four loads in flight, and counts the low digit in its
+    // warp's histogram; equal digits may then land in any order (returned atomics), since the
+    // later passes are stable.
+    for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
+    __syncwarp();
+    for (int i0 = tid; i0 < area; i0 += 4 * nthreads) {
+        uint32_t key[4];
+        bool in[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k * nthreads;
+            in[k] = i < area && inside(i);
+            key[k] = 0;
+            if (in[k]) {
+                const int v = (int)__umulhi((unsigned)i, P.div_magic);
+                key[k] = Traits<DT>::key(load_px<DT>(im, gx0 + i - v * S, gy0 + v));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (in[k]) {
+                keys[i0 + k * nthreads] = key[k];
+                atomicAdd(&hw[key[k] & 0xff], 1u);
+            }
     }
     G.sync();
-    const int area = S * P.SH;
-    const Pos* src = nullptr;
-    Pos* dst = bufA;
+    scan_counts();
+    G.sync();
+    for (int i = tid; i < area; i += nthreads)
+        if (inside(i)) bufA[atomicAdd(&hw[keys[i] & 0xff], 1u)] = (Pos)i;
+    G.sync();
+    // stable passes over the current order: each warp owns one contiguous segment; a pixel's
+    // new place is its (digit, warp)-major exclusive offset plus its position among equal
+    // digits earlier in the segment (warp match)
+    const Pos* src = bufA;
+    Pos* dst = bufB;
     constexpr int kPasses = DT == FIM_F32 ? 4 : 2;  // 8-bit digits of 32- or 16-bit keys
     static_assert(kPasses % 2 == 0, "the sorted positions must end in list B");
-    for (int pass = 0; pass < kPasses; ++pass) {
+    const int N = P.N;
+    const int seg = ((N + nwarps - 1) / nwarps + 31) & ~31;
+    const int s0 = min(N, warp * seg), s1 = min(N, s0 + seg);
+    for (int pass = 1; pass < kPasses; ++pass) {
         const int shift = 8 * pass;
-        const int len = pass == 0 ? area : P.N;
-        const int seg = ((len + nwarps - 1) / nwarps + 31) & ~31;
-        const int s0 = min(len, warp * seg), s1 = min(len, s0 + seg);
-        uint32_t* hw = hist + warp * HS;
         for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
         __syncwarp();
-        for (int b = s0; b < s1; b += 32) {
-            const int i = b + lane;
-            bool valid = i < s1;
-            int pos = 0;
-            if (valid) {
-                if (pass == 0) {
-                    const int v = (int)__umulhi((unsigned)i, P.div_magic);
-                    const int u = i - v * S;
-                    const int fr = frow[v];
-                    valid = u >= span_lo(fr) && u <= span_hi(fr);
-                    pos = i;
-                } else {
-                    pos = (int)src[i];
-                }
-            }
-            const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
-            if (pass == 0) {  // the first pass need not be stable: plain shared-memory counts
-                if (valid) atomicAdd(&hw[d], 1u);
-            } else {
-                const uint32_t peers = __match_any_sync(kFull, d);
-                if (valid && lane == __ffs(peers) - 1) hw[d] += __popc(peers);
-                __syncwarp();
-            }
-        }
+        for (int i = s0 + lane; i < s1; i += 32)  // counts do not depend on the order
+            atomicAdd(&hw[(keys[src[i]] >> shift) & 0xff], 1u);
         G.sync();
-        {   // exclusive scan in (digit, warp) order: each thread takes 8 consecutive counters
-            const int e0 = tid * 8;  // 256 * nwarps counters over 32 * nwarps threads
-            uint32_t c[8];
-            uint32_t local = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int e = e0 + j, d = e / nwarps, wq = e - d * nwarps;
-                c[j] = hist[wq * HS + d];
-                local += c[j];
-            }
-            uint32_t incl = local;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            if (lane == 31) wsum[warp] = incl;
-            G.sync();
-            if (warp == 0) {
-                const uint32_t x = lane < nwarps ? wsum[lane] : 0;
-                uint32_t y = x;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(kFull, y, o);
-                    if (lane >= o) y += t;
-                }
-                wsum[lane] = y - x;
-            }
-            G.sync();
-            uint32_t run = incl - local + wsum[warp];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int e = e0 + j, d = e / nwarps, wq = e - d * nwarps;
-                hist[wq * HS + d] = run;
-                run += c[j];
-            }
-        }
+        scan_counts();
         G.sync();
         for (int b = s0; b < s1; b += 32) {
             const int i = b + lane;
-            bool valid = i < s1;
-            int pos = 0;
-            if (valid) {
-                if (pass == 0) {
-                    const int v = (int)__umulhi((unsigned)i, P.div_magic);
-                    const int u = i - v * S;
-                    const int fr = frow[v];
-                    valid = u >= span_lo(fr) && u <= span_hi(fr);
-                    pos = i;
-                } else {
-                    pos = (int)src[i];
-                }
-            }
+            const bool valid = i < s1;
+            const int pos = valid ? (int)src[i] : 0;
             const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
-            if (pass == 0) {  // equal digits may land in any order: the next passes are stable
-                if (valid) dst[atomicAdd(&hw[d], 1u)] = (Pos)pos;
-                continue;
-            }
             const uint32_t peers = __match_any_sync(kFull, d);
             uint32_t base = 0;
             if (valid) base = hw[d];
@@ -583,7 +585,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     }
     // an even number of passes: the sorted positions are in B; rewrite them in place as entries
     typename Loc<W>::E* om = reinterpret_cast<typename Loc<W>::E*>(bufB);
-    for (int v = tid; v < P.N; v += nthreads) {
+    for (int v = tid; v < N; v += nthreads) {
         const int pos = (int)bufB[v];
         const int y = (int)__umulhi((unsigned)pos, P.div_magic);
         om[v] = Loc<W>::pack(pos - y * S, y, P.cx0, P.cy0);
