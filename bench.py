@@ -145,7 +145,8 @@ class ClockSampler:
 
 def algorithmic_ops_per_pixel(r: int, footprint: int, tile_w: int, tile_h: int, passes: int = 1) -> float:
     """Element operations per output pixel of the disk filter: the ordinal transform touches
-    every footprint pixel once per sort pass (counting sort: one pass for 8/16-bit data), a
+    every footprint pixel once per sort pass (16-bit data: one counting-sort pass in 1024-thread
+    CTAs, two radix passes in smaller ones), a
     vertical slide compares the 2*(2r+1) entering and leaving pixels, and the omnigram
     refinement tests at least one 32-entry block. Each element operation needs at least one
     integer instruction."""
@@ -158,7 +159,7 @@ def peak_alu_ops(clock_mhz: float) -> float:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("fim_tile.cu", "fim_internal.h", "fim_host.cu"):
+    for name in ("fim_tile_pipeline.cuh", "fim_tile.cu", "fim_internal.h", "fim_host.cu"):
         p = os.path.join(ROOT, "paper_2505_22938_gb300", "csrc", name)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -524,7 +525,8 @@ def run_native(args):
         lm = [l[i] for l in launch_ms]
         avg = sum(lm) / len(lm)
         plan = fim.fim_plan_info(kernels[i], fim.FIM_U16, W, H)
-        ops = algorithmic_ops_per_pixel(r, plan["footprint"], plan["tile_w"], plan["tile_h"]) * H * W
+        passes = 1 if plan["threads"] >= 1024 else 2  # 16-bit counting sort, or two radix passes
+        ops = algorithmic_ops_per_pixel(r, plan["footprint"], plan["tile_w"], plan["tile_h"], passes) * H * W
         tot_ops += ops
         tot_ms += avg
         per_radius[f"r{r}"] = {"ms": round(avg, 4), "Mpix_s": round(H * W / avg / 1e3, 1),

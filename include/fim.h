@@ -129,8 +129,13 @@ fim_status fim_percentile(const void* in, void* out, int w, int h, size_t pitch_
 
 /*
  * fim_median with HOST buffers: copies the input to the device, filters, copies the result
- * back, and returns when the output is in `out_host`. Device buffers are allocated on
- * first use and cached per thread. Rows are pitch_bytes apart in both host buffers.
+ * back, and returns when the output is in `out_host`. Device buffers (and, for images of
+ * several tile rows, three streams and their events) are allocated on first use and cached
+ * per thread. The image is processed in up to 8 bands of whole tile rows: a band's input rows
+ * (with the kernel's reach) are copied in, its tiles filtered and its rows copied out while
+ * the next bands proceed, so the copies overlap the filtering; with pinned host buffers the
+ * copies are asynchronous. The caller's stream waits for the whole pipeline before the call
+ * returns. Rows are pitch_bytes apart in both host buffers.
  */
 fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, size_t pitch_bytes,
                            fim_dtype dtype, const fim_kernel* k, fim_border border, void* stream);

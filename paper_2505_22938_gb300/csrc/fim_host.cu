@@ -369,8 +369,8 @@ static bool parse_tile_env(TileShape* ts) {
 }
 
 fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int cta_threads) {
-    static const TileShape cands[] = {{32, 32, 2, 1}, {64, 128, 8, 2}, {64, 64, 8, 2}, {32, 64, 8, 2},
-                                      {32, 32, 8, 2}, {32, 16, 8, 2}};
+    static const TileShape cands[] = {{32, 32, 2, 1}, {32, 32, 4, 1}, {64, 128, 8, 2}, {64, 64, 8, 2},
+                                      {32, 64, 8, 2}, {32, 32, 8, 2}, {32, 16, 8, 2}};
     TileShape forced;
     if (parse_tile_env(&forced)) {  // explicit override (experiments, tuning)
         Plan* p = new (std::nothrow) Plan;
@@ -395,14 +395,13 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
             return FIM_OK;
         }
     }
-    // Defaults measured on the 4096^2 photo-like workload. Kernels up to 25 pixels across (33
-    // for 8-bit data): small tiles (the footprint, and so every refinement scan, shrinks with
-    // the tile) in 128-thread CTAs, many per SM (16-bit data then sorts by radix passes); up to
-    // 80 across: 64x64 tiles in 1024-thread CTAs; beyond: taller 64x128 tiles, which halve the
-    // seed and seed-row work per pixel.
+    // Defaults measured on the 4096^2 photo-like workload. Kernels up to 33 pixels across: 32x32
+    // tiles with two bands in 128-thread CTAs, many per SM (the footprint, and so every
+    // refinement scan, shrinks with the tile; 16-bit data then sorts by radix passes); up to 45
+    // across: the same tiles with four bands; up to 80 across: 64x64 tiles in 1024-thread CTAs;
+    // beyond: taller 64x128 tiles, which halve the seed and seed-row work per pixel.
     const int extent = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1;
-    const int small_limit = dtype == FIM_U8 ? 33 : 25;
-    const int first = extent <= small_limit ? 0 : (extent >= 81 ? 1 : 2);
+    const int first = extent <= 33 ? 0 : (extent <= 45 ? 1 : (extent >= 81 ? 2 : 3));
     for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
         const TileShape& c = cands[i];
         Plan* p = new (std::nothrow) Plan;
@@ -451,6 +450,29 @@ struct Hostbufs {
     ~Hostbufs() {
         if (d_in) cudaFree(d_in);
         if (d_out) cudaFree(d_out);
+    }
+};
+
+// Streams and events of the banded host pipeline (one set per host thread).
+constexpr int kHostBands = 8;
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr, comp[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr, done = nullptr, in_ev[kHostBands] = {}, comp_ev[kHostBands] = {};
+    bool ready = false;
+    bool init() {
+        if (ready) return true;
+        bool ok = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&comp[0], cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&comp[1], cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess;
+        for (int b = 0; ok && b < kHostBands; ++b)
+            ok = cudaEventCreateWithFlags(&in_ev[b], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&comp_ev[b], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        ready = ok;
+        return ok;
     }
 };
 
@@ -640,6 +662,7 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
     fim_status s = check_image_args(in_host, out_host, w, h, pitch_bytes, dtype, k, border);
     if (s != FIM_OK) return s;
     static thread_local Hostbufs bufs;
+    static thread_local HostPipe pipe;
     const size_t es = (size_t)elem_size(dtype);
     const size_t dpitch = (size_t)w * es;
     const size_t bytes = dpitch * (size_t)h;
@@ -655,14 +678,85 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
         bufs.bytes = bytes;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpy2DAsync(bufs.d_in, dpitch, in_host, pitch_bytes, dpitch, h, cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-        return FIM_ERR_CUDA;
-    s = filter_rank(bufs.d_in, bufs.d_out, w, h, dpitch, dtype, k, (k->n - 1) / 2, st);
+    const int limit = device_smem_limit();
+    if (limit <= 0) return FIM_ERR_CUDA;
+    TileShape ts;
+    s = choose_tile(k, dtype, limit, &ts);
     if (s != FIM_OK) return s;
-    if (cudaMemcpy2DAsync(out_host, pitch_bytes, bufs.d_out, dpitch, dpitch, h, cudaMemcpyDeviceToHost, st) !=
-        cudaSuccess)
+    Plan* p = new (std::nothrow) Plan;
+    if (!p) return FIM_ERR_OOM;
+    s = make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, limit, p);
+    if (s != FIM_OK) {
+        delete p;
+        return s;
+    }
+    p->in = bufs.d_in;
+    p->out = bufs.d_out;
+    p->pitch = (long long)dpitch;
+    // Bands of whole tile rows: band b's input rows (its rows plus the kernel's reach below)
+    // are copied in, its tiles filtered on one of two compute streams (a band's tail overlaps
+    // the next band's start) and its rows copied out, so the copies hide behind the kernels.
+    const int rows_per_band = (p->tiles_y + kHostBands - 1) / kHostBands;
+    const int bands = (p->tiles_y + rows_per_band - 1) / rows_per_band;
+    const char* hin = static_cast<const char*>(in_host);
+    char* hout = static_cast<char*>(out_host);
+    const char* din = static_cast<const char*>(bufs.d_in);
+    const char* dout = static_cast<const char*>(bufs.d_out);
+    auto fail = [&]() {
+        cudaGetLastError();
+        delete p;
         return FIM_ERR_CUDA;
+    };
+    if (bands < 2 || !pipe.init()) {  // one band: copy in, filter, copy out on the caller's stream
+        if (cudaMemcpy2DAsync(bufs.d_in, dpitch, in_host, pitch_bytes, dpitch, h, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+            return fail();
+        s = launch_tile_kernel(*p, st);
+        if (s == FIM_OK && cudaMemcpy2DAsync(out_host, pitch_bytes, bufs.d_out, dpitch, dpitch, h,
+                                             cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return fail();
+    } else {
+        if (cudaEventRecord(pipe.start, st) != cudaSuccess || cudaStreamWaitEvent(pipe.in, pipe.start, 0) != cudaSuccess)
+            return fail();
+        int copied = 0;  // input rows already on the device
+        for (int b = 0; b < bands && s == FIM_OK; ++b) {
+            const int tr0 = b * rows_per_band, tr1 = std::min(p->tiles_y, tr0 + rows_per_band);
+            const int y0 = tr0 * p->Ty, y1 = std::min(h, tr1 * p->Ty);
+            const int need = std::min(h, y1 + p->ymax);  // rows [0, need) feed this band
+            if (need > copied) {
+                if (cudaMemcpy2DAsync((void*)(din + (size_t)copied * dpitch), dpitch,
+                                      hin + (size_t)copied * pitch_bytes, pitch_bytes, dpitch, need - copied,
+                                      cudaMemcpyHostToDevice, pipe.in) != cudaSuccess)
+                    return fail();
+                copied = need;
+            }
+            cudaStream_t cs = pipe.comp[b & 1];
+            if (cudaEventRecord(pipe.in_ev[b], pipe.in) != cudaSuccess ||
+                cudaStreamWaitEvent(cs, pipe.in_ev[b], 0) != cudaSuccess)
+                return fail();
+            Plan& band = *p;
+            band.tile0 = tr0 * p->tiles_x;
+            band.tile_count = (tr1 - tr0) * p->tiles_x;
+            s = launch_tile_kernel(band, cs);
+            if (s != FIM_OK) {  // nothing may still be writing the caller's buffers on return
+                cudaStreamSynchronize(pipe.in);
+                cudaStreamSynchronize(pipe.comp[0]);
+                cudaStreamSynchronize(pipe.comp[1]);
+                cudaStreamSynchronize(pipe.out);
+                break;
+            }
+            if (cudaEventRecord(pipe.comp_ev[b], cs) != cudaSuccess ||
+                cudaStreamWaitEvent(pipe.out, pipe.comp_ev[b], 0) != cudaSuccess ||
+                cudaMemcpy2DAsync(hout + (size_t)y0 * pitch_bytes, pitch_bytes, dout + (size_t)y0 * dpitch, dpitch,
+                                  dpitch, y1 - y0, cudaMemcpyDeviceToHost, pipe.out) != cudaSuccess)
+                return fail();
+        }
+        if (s == FIM_OK && (cudaEventRecord(pipe.done, pipe.out) != cudaSuccess ||
+                            cudaStreamWaitEvent(st, pipe.done, 0) != cudaSuccess))
+            return fail();
+    }
+    delete p;
+    if (s != FIM_OK) return s;
     if (cudaStreamSynchronize(st) != cudaSuccess) return FIM_ERR_CUDA;
     return FIM_OK;
 }

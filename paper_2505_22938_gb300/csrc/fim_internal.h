@@ -105,7 +105,8 @@ struct Plan {
     int smem_bytes;
     long long scratch_per_cta;  // bytes of global scratch per resident CTA (multiple of 256)
     // persistent grid
-    int ntiles;                 // tiles_x * tiles_y
+    int ntiles;                 // tiles of this launch
+    int tile0, tile_count;      // single-image launches: tiles [tile0, tile0 + tile_count) (count 0: all)
     unsigned char* scratch;     // header (256 B: tile counter) + grid * scratch_per_cta
     // tables (copied to shared memory at kernel start)
     int frow[kMaxSide];                   // footprint row v covers u in [lo, hi]: lo | hi << 16

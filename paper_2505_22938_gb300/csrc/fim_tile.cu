@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
         const int tile = s_tile;
         if (tile >= P.ntiles) break;
         stamp(P, tile, 0, G);
-        process_tile<DT, SHAPE, W, OG>(P, tile, gslice, G);
+        process_tile<DT, SHAPE, W, OG>(P, P.tile0 + tile, gslice, G);
     }
 }
 
@@ -37,7 +37,7 @@ fim_status launch_typed(Plan& p, cudaStream_t stream) {
         cudaGetLastError();
         return FIM_ERR_UNSUPPORTED;
     }
-    const long long tiles = (long long)p.tiles_x * p.tiles_y;
+    const long long tiles = p.tile_count > 0 ? (long long)p.tile_count : (long long)p.tiles_x * p.tiles_y;
     if (tiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
     p.ntiles = (int)tiles;
     const int grid = (int)std::min<long long>(tiles, (long long)occ * device_sm_count());
