@@ -148,9 +148,9 @@ def algorithmic_ops_per_pixel(r: int, footprint: int, tile_w: int, tile_h: int, 
     every footprint pixel once per sort pass (16-bit data: one counting-sort pass in 1024-thread
     CTAs, two radix passes in smaller ones), a
     vertical slide compares the 2*(2r+1) entering and leaving pixels, and the omnigram
-    refinement tests at least one 32-entry block. Each element operation needs at least one
-    integer instruction."""
-    return footprint / (tile_w * tile_h) * passes + 2 * (2 * r + 1) + 32
+    refinement tests at least one 64-entry block (the minimum when the median stays within its
+    pivot quantum). Each element operation needs at least one integer instruction."""
+    return footprint / (tile_w * tile_h) * passes + 2 * (2 * r + 1) + 64
 
 
 def peak_alu_ops(clock_mhz: float) -> float:
@@ -538,7 +538,7 @@ def run_native(args):
                 "frac": achieved / peak, "traffic": profiled_traffic(),
                 "kernel": "tile_median_kernel<u16,disk>",
                 "peak_note": "instruction-issue peak: 152 SMs x 128 lanes/clk x max SM clock; ops = algorithmic "
-                             "element operations (sort key-passes + slide compares + 32 refine tests per pixel)"}
+                             "element operations (sort key-passes + slide compares + 64 refine tests per pixel)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
