@@ -48,6 +48,16 @@ def test_u16_sort_paths(tile, r, monkeypatch):
     run_case(np.ascontiguousarray(img), "circle", r)
 
 
+@pytest.mark.parametrize("tile", ["32,32,2,1", "32,64,4,1"])
+@pytest.mark.parametrize("dtype", ["u16", "f32"])
+def test_radix_small_cta_wide_box(tile, dtype, monkeypatch):
+    """Radix sort in a small CTA with a footprint box wider than 255 (32-bit entries and
+    positions, lists in the CTA's global slice)."""
+    monkeypatch.setenv("FIM_TILE", tile)
+    img = datagen.image_for(dtype, datagen.seed_for(3, 11), 97, 83)
+    run_case(img, "circle", 115)
+
+
 @pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
 @pytest.mark.parametrize("r", [5, 21])
 def test_dtypes_ragged(dtype, r):
