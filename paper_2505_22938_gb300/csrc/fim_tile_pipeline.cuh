@@ -244,13 +244,14 @@ __device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, in
 }
 
 // Per-thread exact selection (vertical sweep): every lane refines its own window. It scans the
-// omnigram from its pivot in aligned groups of entries (one 128-bit load), counting members,
-// until the group holding the target-th member. While at least kHandoff lanes are still
+// omnigram from its pivot in aligned groups of entries (one 128-bit load), two groups per step
+// (the loop's votes and bookkeeping are paid once per two groups), counting members, until the
+// group holding the target-th member. While at least kHandoff lanes are still
 // scanning this is the cheapest schedule; the last few lanes of a warp (long jumps at edges and
 // impulses) are finished by warp-cooperative ballot scans instead of keeping 29+ lanes idle.
 // Same contract as ballot_select, per lane. All loops are bounded by the omnigram length.
 constexpr int kHandoff = 8;
-constexpr int kHandoffAfter = 12;  // groups
+constexpr int kHandoffAfter = 6;  // steps of two groups
 
 template <int SHAPE, int W>
 __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
@@ -281,23 +282,36 @@ __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restric
             if ((unsigned)g > (unsigned)glast) {
                 done = true;
             } else {
+                // two groups per step: the second (further from the pivot) when it exists
+                const int g2 = up ? g + 1 : g - 1;
+                const bool has2 = (unsigned)g2 <= (unsigned)glast;
                 const uint4 q = om128[g];
+                const uint4 q2 = om128[has2 ? g2 : g];
                 constexpr int kb = G / 4;  // entries per word
                 uint32_t mask = (wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb))) & first;
+                uint32_t mask2 = wt(q2.x) | (wt(q2.y) << kb) | (wt(q2.z) << (2 * kb)) | (wt(q2.w) << (3 * kb));
+                if (!has2) mask2 = 0;
                 first = kAll;
                 const int cnt = __popc(mask);
-                if (cnt >= need) {
+                int gg = g;
+                if (cnt < need) {
+                    need -= cnt;
+                    mask = mask2;
+                    gg = g2;
+                }
+                const int cnt2 = __popc(mask);
+                if (cnt2 >= need) {
                     if (up) {
                         for (int k = 1; k < need; ++k) mask &= mask - 1;  // drop the lowest need-1
-                        m = G * g + __ffs(mask) - 1;
+                        m = G * gg + __ffs(mask) - 1;
                     } else {
                         for (int k = 1; k < need; ++k) mask ^= 1u << (31 - __clz(mask));  // drop the highest
-                        m = G * g + 31 - __clz(mask);
+                        m = G * gg + 31 - __clz(mask);
                     }
                     done = true;
                 } else {
-                    need -= cnt;
-                    nextv = up ? G * g + G : G * g - 1;
+                    need -= cnt2;
+                    nextv = up ? G * g2 + G : G * g2 - 1;
                 }
             }
         }
