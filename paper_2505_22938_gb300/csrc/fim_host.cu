@@ -188,6 +188,9 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->G = ts.G;
     p->vthreads = 2 * ts.Tx * ts.RB;
     p->threads = std::max(p->vthreads, cta_threads);
+    // Scans are short in the small tiles of small kernels (4 groups per step) and long in the
+    // large tiles (8): measured on the 4096^2 photo-like workload, each within 2 % of the best.
+    p->scan_groups = p->vthreads < 1024 ? 4 : 8;
     p->nwarps = p->threads / 32;
     if (p->threads > 1024 || p->threads % 32 != 0) return FIM_ERR_INTERNAL;
     p->shape = k->shape;
@@ -208,7 +211,8 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->S = ts.Tx + (k->xmax - k->xmin);
     p->SH = ts.Ty + (k->ymax - k->ymin);
     if (p->S > kMaxSide || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
-    p->wide = (p->S > 255 || p->SH > 255) ? 1 : 0;  // 8-bit coordinates keep -128 free
+    // 8-bit coordinates need one axis that never reaches -128, which marks the padding entries
+    p->wide = (p->S > 256 || p->SH > 256 || (p->S == 256 && p->SH == 256)) ? 1 : 0;
     p->SP = (p->S + 1) & ~1;
     if ((p->SP / 2) % 2 == 0) p->SP += 2;  // odd number of 32-bit words per row: no bank aliasing
     p->tiles_x = (w + ts.Tx - 1) / ts.Tx;

@@ -24,7 +24,7 @@
 // below the pivot is exactly the target rank, and a slide only adds the change.
 //
 // W selects the omnigram encoding: W = 0 packs a location as two int8 coordinates (footprint
-// box up to 255 x 255, Sec. 4.1; -128 marks padding); W = 1 uses two int16 coordinates. OG = 1
+// box up to 256 x 256 with one side below 256, Sec. 4.1; -128 marks padding); W = 1 uses int16. OG = 1
 // keeps the omnigram in the CTA's global scratch slice when shared memory cannot hold it.
 #include <stdint.h>
 
@@ -72,7 +72,7 @@ struct Loc<0> {
     using E = uint16_t;    // entry
     using Pos = uint16_t;  // bounding-box position in the radix lists
     static constexpr int kGroup = 8;  // entries per 128-bit load
-    static constexpr E kSentinel = 0x8080;  // (-128, -128): outside every window of a box < 256
+    static constexpr E kSentinel = 0x8080;  // (-128, -128): a box side below 256 keeps it out of every window
     __device__ static E pack(int u, int v, int cx0, int cy0) {
         return (E)((uint32_t)(uint8_t)(int8_t)(u - cx0) | ((uint32_t)(uint8_t)(int8_t)(v - cy0) << 8));
     }
@@ -244,18 +244,20 @@ __device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, in
 }
 
 // Per-thread exact selection (vertical sweep): every lane refines its own window. It scans the
-// omnigram from its pivot in aligned groups of entries (one 128-bit load), two groups per step
-// (the loop's votes and bookkeeping are paid once per two groups), counting members, until the
-// group holding the target-th member. While at least kHandoff lanes are still
+// omnigram from its pivot in aligned groups of entries (one 128-bit load), K groups per step
+// (the loop's votes and bookkeeping are paid once per K groups: K = 4 where scans are short,
+// small kernels; 8 where they are long), counting members, until the group holding the
+// target-th member. While at least kHandoff lanes are still
 // scanning this is the cheapest schedule; the last few lanes of a warp (long jumps at edges and
 // impulses) are finished by warp-cooperative ballot scans instead of keeping 29+ lanes idle.
 // Same contract as ballot_select, per lane. All loops are bounded by the omnigram length.
 constexpr int kHandoff = 8;
-constexpr int kHandoffAfter = 6;  // steps of two groups
+constexpr int kHandoffAfterGroups = 12;
 
-template <int SHAPE, int W>
+template <int SHAPE, int W, int K>
 __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
                                              int target, int px, int py, const Member<SHAPE, W>& member) {
+    constexpr int handoff_after = (kHandoffAfterGroups + K - 1) / K;  // steps
     constexpr int G = Loc<W>::kGroup;
     constexpr uint32_t kAll = (1u << G) - 1;
     const int lane = threadIdx.x & 31;
@@ -275,43 +277,49 @@ __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restric
     constexpr int kShift = G == 8 ? 3 : 2;
     for (int it = 0; it <= glast + 1; ++it) {
         // the hand-off test costs a vote, so it only starts once the typical scan is over
-        if (it >= kHandoffAfter && __popc(__ballot_sync(kFull, !done)) < kHandoff) break;
-        if (it < kHandoffAfter && !__any_sync(kFull, !done)) break;
+        if (it >= handoff_after && __popc(__ballot_sync(kFull, !done)) < kHandoff) break;
+        if (it < handoff_after && !__any_sync(kFull, !done)) break;
         if (!done) {
             const int g = nextv >> kShift;  // -1 below entry 0
             if ((unsigned)g > (unsigned)glast) {
                 done = true;
             } else {
-                // two groups per step: the second (further from the pivot) when it exists
-                const int g2 = up ? g + 1 : g - 1;
-                const bool has2 = (unsigned)g2 <= (unsigned)glast;
-                const uint4 q = om128[g];
-                const uint4 q2 = om128[has2 ? g2 : g];
                 constexpr int kb = G / 4;  // entries per word
-                uint32_t mask = (wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb))) & first;
-                uint32_t mask2 = wt(q2.x) | (wt(q2.y) << kb) | (wt(q2.z) << (2 * kb)) | (wt(q2.w) << (3 * kb));
-                if (!has2) mask2 = 0;
-                first = kAll;
-                const int cnt = __popc(mask);
-                int gg = g;
-                if (cnt < need) {
-                    need -= cnt;
-                    mask = mask2;
-                    gg = g2;
+                uint32_t selmask = 0;
+                int selg = 0;
+                bool found = false;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int gk = up ? g + k : g - k;
+                    const bool ok = (unsigned)gk <= (unsigned)glast;
+                    const uint4 q = om128[ok ? gk : g];
+                    uint32_t mk = wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb));
+                    if (!ok) mk = 0;
+                    if (k == 0) mk &= first;
+                    const int c = __popc(mk);
+                    if (!found) {
+                        if (c >= need) {
+                            found = true;
+                            selmask = mk;
+                            selg = gk;
+                        } else {
+                            need -= c;
+                        }
+                    }
                 }
-                const int cnt2 = __popc(mask);
-                if (cnt2 >= need) {
+                first = kAll;
+                if (found) {
+                    uint32_t mask = selmask;
                     if (up) {
                         for (int k = 1; k < need; ++k) mask &= mask - 1;  // drop the lowest need-1
-                        m = G * gg + __ffs(mask) - 1;
+                        m = G * selg + __ffs(mask) - 1;
                     } else {
                         for (int k = 1; k < need; ++k) mask ^= 1u << (31 - __clz(mask));  // drop the highest
-                        m = G * gg + 31 - __clz(mask);
+                        m = G * selg + 31 - __clz(mask);
                     }
                     done = true;
                 } else {
-                    need -= cnt2;
-                    nextv = up ? G * g2 + G : G * g2 - 1;
+                    nextv = up ? G * (g + K) : G * (g - K + 1) - 1;
                 }
             }
         }
@@ -1000,6 +1008,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         int cv = t - ymin;
         int p = med[t * TX + s];
         const int ncols = P.ncols;
+        const int scan_groups = P.scan_groups;
         const int eoff = down ? 0 : -SP;
         for (int k = 0; k < steps; ++k) {
             const uint16_t* ctr = ord + cv * SP + cu + eoff;
@@ -1019,7 +1028,9 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             }
             cv += down ? 1 : -1;
             t += down ? 1 : -1;
-            const int mine = thread_select<SHAPE, W>(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
+            const int mine =
+                scan_groups == 8 ? thread_select<SHAPE, W, 8>(om, N, p, target + d, target, cu - cx0, cv - cy0, member)
+                                 : thread_select<SHAPE, W, 4>(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
             if (mine < 0) set_status(FIM_ERR_INTERNAL);
             p = max(mine, 0);
             med[t * TX + s] = (uint16_t)p;

@@ -183,6 +183,15 @@ def test_large_extents(spec):
     run_case(img, *spec)
 
 
+@pytest.mark.parametrize("spec", [("ellipse", 96, 20), ("ellipse", 20, 96), ("circle", 64)])
+@pytest.mark.parametrize("dtype", ["u16", "f32"])
+def test_box_side_256(spec, dtype):
+    """Footprint boxes with one side exactly 256 (8-bit coordinates use the whole range on that
+    axis, so the padding sentinel relies on the other axis) and 256 x 256 (32-bit entries)."""
+    img = datagen.image_for(dtype, 613, 150, 170)
+    run_case(img, *spec)
+
+
 def test_full_size_config3_sampled():
     """8192x8192 f32 (fields + Cauchy outliers) at disk r=64 and 100, the hexagon (R=64) and
     the 80x40 ellipse, in the launch configuration of a full-image call: sampled pixels,
