@@ -402,10 +402,10 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     // Defaults measured on the 4096^2 photo-like workload. Kernels up to 33 pixels across: 32x32
     // tiles with two bands in 128-thread CTAs, many per SM (the footprint, and so every
     // refinement scan, shrinks with the tile; 16-bit data then sorts by radix passes); up to 45
-    // across: the same tiles with four bands; up to 80 across: 64x64 tiles in 1024-thread CTAs;
+    // across: the same tiles with four bands; up to 64 across: 64x64 tiles in 1024-thread CTAs;
     // beyond: taller 64x128 tiles, which halve the seed and seed-row work per pixel.
     const int extent = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1;
-    const int first = extent <= 33 ? 0 : (extent <= 45 ? 1 : (extent >= 81 ? 2 : 3));
+    const int first = extent <= 33 ? 0 : (extent <= 45 ? 1 : (extent >= 65 ? 2 : 3));
     for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
         const TileShape& c = cands[i];
         Plan* p = new (std::nothrow) Plan;
