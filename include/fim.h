@@ -144,9 +144,10 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
  * Tunes the tile configuration for (current device, dtype, kernel geometry): every valid
  * configuration is run on this image (in -> out, which ends up holding the filtered image) and
  * timed with CUDA events; the fastest is kept in a process-wide cache that later fim_median,
- * fim_percentile and batch calls with the same dtype and kernel geometry use. cta_threads = 0
- * tunes over all CTA sizes; 256, 512 or 1024 restricts the search to that CTA size and stores
- * the result separately (batches look up 1024 first: all jobs of a batch share one CTA size).
+ * fim_percentile and batch calls with the same dtype and kernel geometry use (a batch runs a
+ * job's tile groups side by side in 1024-thread CTAs, so the single-image choice carries over).
+ * cta_threads = 0 tunes over all CTA sizes; 256, 512 or 1024 restricts the search to that CTA
+ * size and stores the result separately, for callers that plan with a fixed CTA size.
  * If the environment variable FIM_TUNE_CACHE names a file, the cache is loaded from it on first
  * use and rewritten after each tuning. tile_w / tile_h (may be NULL) receive the chosen tile.
  * Synchronous. Not part of the paper: its GPU tiling is fixed by radius (Sec. 4.2).
@@ -160,8 +161,9 @@ fim_status fim_autotune_clear(void);
 /*
  * Batched persistent launch. One job is one 2-D image filtered with its own kernel, dtype, size
  * and pitch; percentile < 0 selects the median, otherwise the percentile filter of fim_percentile.
- * All tiles of all jobs form one device-side queue worked off by one persistent launch
- * (expensive tiles first). Not part of the paper.
+ * One persistent launch works off every job: each CTA visits the jobs in order of decreasing
+ * cost per tile, and its tile groups (1024 / the job's CTA size of them) take that job's tiles
+ * from the job's own device-side counter until none are left. Not part of the paper.
  */
 typedef struct {
     const void* in;      /* device pointer */
@@ -182,8 +184,8 @@ typedef struct fim_batch fim_batch;
  */
 fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out);
 
-/* Runs a batch on `stream`: one memset of the queue counter and one kernel launch, both stream
- * operations (graph-capturable). Runs of one batch must not overlap in time. */
+/* Runs a batch on `stream`: one memset of the per-job tile counters and one kernel launch, both
+ * stream operations (graph-capturable). Runs of one batch must not overlap in time. */
 fim_status fim_batch_run(fim_batch* b, void* stream);
 
 /* Size of a batch launch: total queued tiles, CTAs, threads per CTA, shared memory per CTA. */

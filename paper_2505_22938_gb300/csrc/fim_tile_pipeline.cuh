@@ -252,7 +252,7 @@ __device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, in
 // impulses) are finished by warp-cooperative ballot scans instead of keeping 29+ lanes idle.
 // Same contract as ballot_select, per lane. All loops are bounded by the omnigram length.
 constexpr int kHandoff = 8;
-constexpr int kHandoffAfterGroups = 12;
+constexpr int kHandoffAfterGroups = 8;
 
 template <int SHAPE, int W, int K>
 __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
