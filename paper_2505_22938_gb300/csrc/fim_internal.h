@@ -174,6 +174,10 @@ void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_device_status(cudaStream_t stream);
 fim_status read_and_clear_batch_status();  // (fim_batch_kernel.cu) called by the above after its sync
+// (fim_tile_k4.cu) the kernels with 4 omnigram groups per scan step, and their status word
+fim_status launch_tile_kernel_k4(Plan& p, cudaStream_t stream);
+fim_status launch_tile_kernel_fixed_k4(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
+fim_status read_and_clear_k4_status();
 fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
 fim_status batch_prepare(int smem);
 fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);

@@ -1,131 +1,25 @@
-// Single-image launches of the tile pipeline: each CTA takes Tx x Ty output tiles from a
-// device-side queue and filters them one after the other (Sec. 3.3, Sec. 4.2).
-#include "fim_tile_pipeline.cuh"
+// Single-image launches with 8 omnigram groups per scan step (the 1024-thread tiles of large
+// kernels) and the dispatch between the two sets of kernels.
+#include "fim_tile_launch.cuh"
 
 namespace fim {
-namespace {
-
-// Persistent CTAs: each takes tiles from the queue counter in the scratch header until none are
-// left. The counter is zeroed on the stream before every launch.
-template <int DT, int SHAPE, int W, int OG>
-__global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_constant__ Plan P) {
-    __shared__ int s_tile;
-    const int tid = threadIdx.x;
-    unsigned char* gslice = P.scratch + 256 + (size_t)blockIdx.x * (size_t)P.scratch_per_cta;
-    load_tables(P);
-    unsigned int* counter = reinterpret_cast<unsigned int*>(P.scratch);
-    const Grp G{tid, tid & 31, tid >> 5, (int)blockDim.x, 0, 0};
-    for (;;) {
-        if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int tile = s_tile;
-        if (tile >= P.ntiles) break;
-        stamp(P, tile, 0, G);
-        process_tile<DT, SHAPE, W, OG>(P, P.tile0 + tile, gslice, G);
-    }
-}
-
-template <int DT, int SHAPE, int W, int OG>
-fim_status launch_typed(Plan& p, cudaStream_t stream) {
-    auto fn = tile_median_kernel<DT, SHAPE, W, OG>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return FIM_ERR_CUDA;
-    }
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p.threads, p.smem_bytes) != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        return FIM_ERR_UNSUPPORTED;
-    }
-    const long long tiles = p.tile_count > 0 ? (long long)p.tile_count : (long long)p.tiles_x * p.tiles_y;
-    if (tiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
-    p.ntiles = (int)tiles;
-    const int grid = (int)std::min<long long>(tiles, (long long)occ * device_sm_count());
-    unsigned char* scratch = nullptr;
-    fim_status s = get_scratch(stream, 256 + (size_t)grid * (size_t)p.scratch_per_cta, &scratch);
-    if (s != FIM_OK) return s;
-    p.scratch = scratch;
-    if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;
-    fn<<<grid, p.threads, p.smem_bytes, stream>>>(p);
-    if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;
-    return FIM_OK;
-}
-
-// Same launch, but on a caller-provided workspace of fixed capacity (no allocation). Returns
-// FIM_ERR_UNSUPPORTED when this launch would need more workspace than `capacity` bytes.
-template <int DT, int SHAPE, int W, int OG>
-fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
-    auto fn = tile_median_kernel<DT, SHAPE, W, OG>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return FIM_ERR_CUDA;
-    }
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, p.threads, p.smem_bytes) != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        return FIM_ERR_UNSUPPORTED;
-    }
-    const long long tiles = (long long)p.tiles_x * p.tiles_y;
-    if (tiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
-    p.ntiles = (int)tiles;
-    const int grid = (int)std::min<long long>(tiles, (long long)occ * device_sm_count());
-    if (256 + (unsigned long long)grid * (unsigned long long)p.scratch_per_cta > capacity) return FIM_ERR_UNSUPPORTED;
-    p.scratch = scratch;
-    if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;  // tile queue counter
-    fn<<<grid, p.threads, p.smem_bytes, stream>>>(p);
-    if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;
-    return FIM_OK;
-}
-
-template <int DT, int SHAPE>
-fim_status launch_w_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
-    if (p.wide) return launch_typed_fixed<DT, SHAPE, 1, 1>(p, scratch, capacity, stream);
-    return p.loc_om < 0 ? launch_typed_fixed<DT, SHAPE, 0, 1>(p, scratch, capacity, stream)
-                        : launch_typed_fixed<DT, SHAPE, 0, 0>(p, scratch, capacity, stream);
-}
-
-template <int DT, int SHAPE>
-fim_status launch_w(Plan& p, cudaStream_t stream) {
-    if (p.wide) return launch_typed<DT, SHAPE, 1, 1>(p, stream);
-    return p.loc_om < 0 ? launch_typed<DT, SHAPE, 0, 1>(p, stream) : launch_typed<DT, SHAPE, 0, 0>(p, stream);
-}
-
-}  // namespace
 
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
-    const bool disk = p.shape == kShapeDisk;
-    switch (p.dtype) {
-        case FIM_U8: return disk ? launch_w<FIM_U8, kShapeDisk>(p, stream) : launch_w<FIM_U8, kShapeSpans>(p, stream);
-        case FIM_U16: return disk ? launch_w<FIM_U16, kShapeDisk>(p, stream) : launch_w<FIM_U16, kShapeSpans>(p, stream);
-        case FIM_F32: return disk ? launch_w<FIM_F32, kShapeDisk>(p, stream) : launch_w<FIM_F32, kShapeSpans>(p, stream);
-    }
-    return FIM_ERR_INVALID_ARG;
+    return p.scan_groups == 4 ? launch_tile_kernel_k4(p, stream) : launch_tile_kernel_ks<8>(p, stream);
 }
 
 fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
-    const bool disk = p.shape == kShapeDisk;
-    switch (p.dtype) {
-        case FIM_U8:
-            return disk ? launch_w_fixed<FIM_U8, kShapeDisk>(p, scratch, capacity, stream)
-                        : launch_w_fixed<FIM_U8, kShapeSpans>(p, scratch, capacity, stream);
-        case FIM_U16:
-            return disk ? launch_w_fixed<FIM_U16, kShapeDisk>(p, scratch, capacity, stream)
-                        : launch_w_fixed<FIM_U16, kShapeSpans>(p, scratch, capacity, stream);
-        case FIM_F32:
-            return disk ? launch_w_fixed<FIM_F32, kShapeDisk>(p, scratch, capacity, stream)
-                        : launch_w_fixed<FIM_F32, kShapeSpans>(p, scratch, capacity, stream);
-    }
-    return FIM_ERR_INVALID_ARG;
+    return p.scan_groups == 4 ? launch_tile_kernel_fixed_k4(p, scratch, capacity, stream)
+                              : launch_tile_kernel_fixed_ks<8>(p, scratch, capacity, stream);
 }
 
 fim_status read_and_clear_device_status(cudaStream_t stream) {
-    int v = 0;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return FIM_ERR_CUDA;
-    if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return FIM_ERR_CUDA;
-    const int zero = 0;
-    if (v != 0 && cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return FIM_ERR_CUDA;
-    const fim_status b = read_and_clear_batch_status();  // the batch kernel's own word
-    return v != 0 ? (fim_status)v : b;
+    // every translation unit with device code has its own status word: report the first error
+    const fim_status a = read_and_clear_unit_status();
+    const fim_status b = read_and_clear_k4_status();
+    const fim_status c = read_and_clear_batch_status();
+    return a != FIM_OK ? a : (b != FIM_OK ? b : c);
 }
 
 }  // namespace fim

@@ -254,10 +254,15 @@ __device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, in
 constexpr int kHandoff = 8;
 constexpr int kHandoffAfterGroups = 8;
 
-template <int SHAPE, int W, int K>
+// KS > 0: KS groups per step, fixed at compile time; KS = 0: `groups` per step (at most 8),
+// read at run time (smaller code, for the batch kernel that serves every plan).
+template <int SHAPE, int W, int KS>
 __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
-                                             int target, int px, int py, const Member<SHAPE, W>& member) {
-    constexpr int handoff_after = (kHandoffAfterGroups + K - 1) / K;  // steps
+                                             int target, int px, int py, const Member<SHAPE, W>& member,
+                                             int groups = KS) {
+    constexpr int kUnroll = KS > 0 ? KS : 8;
+    const int K = KS > 0 ? KS : groups;
+    const int handoff_after = (kHandoffAfterGroups + K - 1) / K;  // steps
     constexpr int G = Loc<W>::kGroup;
     constexpr uint32_t kAll = (1u << G) - 1;
     const int lane = threadIdx.x & 31;
@@ -289,7 +294,8 @@ __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restric
                 int selg = 0;
                 bool found = false;
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
+                for (int k = 0; k < kUnroll; ++k) {
+                    if (KS == 0 && k >= K) break;  // uniform: every lane has the same K
                     const int gk = up ? g + k : g - k;
                     const bool ok = (unsigned)gk <= (unsigned)glast;
                     const uint4 q = om128[ok ? gk : g];
@@ -712,7 +718,10 @@ __device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, 
     return reinterpret_cast<T*>(loc >= 0 ? smem + loc : gslice + (-(long long)loc - 1));
 }
 
-template <int DT, int SHAPE, int W, int OG>
+// KS: omnigram groups per scan step of the vertical sweep, fixed at compile time (4 or 8), or
+// 0 to follow the plan's scan_groups at run time (the batch kernel, which serves every plan:
+// one run-time loop keeps its 18 inlined pipelines small enough to compile quickly).
+template <int DT, int SHAPE, int W, int OG, int KS = 0>
 __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G) {
     extern __shared__ __align__(16) unsigned char smem_base[];
     unsigned char* const smem = smem_base + G.shift;  // this group's partition (tables excluded)
@@ -1028,9 +1037,8 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             }
             cv += down ? 1 : -1;
             t += down ? 1 : -1;
-            const int mine =
-                scan_groups == 8 ? thread_select<SHAPE, W, 8>(om, N, p, target + d, target, cu - cx0, cv - cy0, member)
-                                 : thread_select<SHAPE, W, 4>(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
+            int mine;
+            mine = thread_select<SHAPE, W, KS>(om, N, p, target + d, target, cu - cx0, cv - cy0, member, scan_groups);
             if (mine < 0) set_status(FIM_ERR_INTERNAL);
             p = max(mine, 0);
             med[t * TX + s] = (uint16_t)p;
