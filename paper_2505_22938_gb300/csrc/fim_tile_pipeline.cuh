@@ -1,14 +1,16 @@
 #pragma once
-// Per-tile median kernel: each CTA takes Tx x Ty output tiles from a device-side queue and
-// filters them one after the other (Sec. 3.3, Sec. 4.2).
+// The tile pipeline: one Tx x Ty output tile filtered by one tile group (a CTA, or part of a
+// batch CTA) (Sec. 3.3, Sec. 4.2). The single-image and batch kernels include this file.
 //
-// Phases of one tile, separated by __syncthreads():
+// Phases of one tile, separated by group barriers:
 //   1. ordinal transform - the rounded-rectangle footprint (Fig. 10) is read with clamp-to-edge
 //                        and key-value sorted by value, giving the omnigram Omega (Sec. 3.3):
-//                          8/16-bit data: counting sort over 256 / 65536 shared-memory bins, the
-//                                         bucket construction of Eq. 5 run by all threads;
-//                          float data:    stable LSD radix sort of order-preserving keys
-//                                         (Sec. 4.1 float key), four 8-bit passes.
+//                          8-bit, and 16-bit data in 1024-thread CTAs: counting sort over 256 /
+//                                         65536 shared-memory bins, the bucket construction of
+//                                         Eq. 5 run by all threads;
+//                          float, and 16-bit data in smaller CTAs: LSD radix sort of
+//                                         order-preserving keys (Sec. 4.1 float key), 8-bit
+//                                         passes (four / two).
 //   2. ordinal image   - I(Omega[v]) = v (Eq. 4), exact 16-bit ranks.
 //   3. seed solve      - RB*G seed windows, one warp each: coarse histogram of I over the
 //                        window, then a ballot scan of Omega to the exact median (Sec. 4.2).
@@ -17,15 +19,17 @@
 //   4. seed rows       - one warp per (seed, direction) slides the window left/right; lanes
 //                        split the kernel rows and reduce the count change (Sec. 3.3 step 4).
 //   5. vertical sweep  - one thread per (column, band, direction) slides its window up or
-//                        down (Fig. 7) and refines it by scanning Omega itself; the last few
-//                        lanes of a warp hand their long scans to warp ballots (Sec. 4.1, Eq. 2).
+//                        down (Fig. 7) and refines it by scanning Omega itself, K 128-bit
+//                        groups per step; the last few lanes of a warp hand their long scans to
+//                        warp ballots (Sec. 4.1, Eq. 2).
 //   6. output          - out = C[m] through the omnigram: the input value at Omega[m].
 // Pivots are exact previous medians (Huang's choice, Sec. 3.1): after each solve the count
 // below the pivot is exactly the target rank, and a slide only adds the change.
 //
 // W selects the omnigram encoding: W = 0 packs a location as two int8 coordinates (footprint
-// box up to 256 x 256 with one side below 256, Sec. 4.1; -128 marks padding); W = 1 uses int16. OG = 1
-// keeps the omnigram in the CTA's global scratch slice when shared memory cannot hold it.
+// box up to 256 x 256 with one side below 256, Sec. 4.1; -128 marks padding); W = 1 uses two
+// int16 coordinates. OG = 1 keeps the omnigram in the CTA's global scratch slice when shared
+// memory cannot hold it.
 #include <stdint.h>
 
 #include <algorithm>
@@ -655,9 +659,10 @@ __device__ __forceinline__ void seed_features(const uint16_t* ord, int SP, const
 // loaded before they are handed to `f`, so the loads of a group overlap instead of each
 // waiting behind the previous group's shared-memory atomics.
 template <class Fn>
-__device__ __forceinline__ void window_walk(const int* spans, int nrows, const uint16_t* ctr, int SP, Fn&& f) {
+__device__ __forceinline__ void window_walk(const int* spans, int nrows, const uint16_t* ctr, int SP, Fn&& f,
+                                            int first = -1, int step = 32) {
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i < nrows; i += 32) {
+    for (int i = first < 0 ? lane : first; i < nrows; i += step) {
         const int sp = spans[i];
         const int width = span_hi(sp) - span_lo(sp) + 1;
         const uint16_t* row = ctr + i * SP + span_lo(sp);
@@ -922,6 +927,31 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 }
             }
             G.sync();  // the next chunk reuses the activation buffers
+        }
+    } else if (P.seed_pairs && P.samples == nullptr && P.stats == nullptr) {
+        // large windows: two warps per seed window, each histogramming every other kernel row
+        // (the seed phase is a latency chain per warp); the first of the pair then adds the
+        // other's counts and refines
+        const int sd = warp >> 1, half = warp & 1;
+        uint32_t* hw = shist + warp * kSeedBins;
+        const int band = sd / P.G, g = sd % P.G;
+        const int s = g * GW + GW / 2, t = band * BH + BH / 2;
+        const int cu = s - xmin, cv = t - ymin;
+        if (sd < nseeds) {
+            for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+            __syncwarp();
+            window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
+                        [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); }, 2 * lane + half, 64);
+        }
+        G.sync();
+        if (sd < nseeds && half == 0) {
+            for (int j = lane; j < kSeedBins; j += 32) hw[j] += hw[kSeedBins + j];
+            __syncwarp();
+            int below = 0;
+            const int pivot = hist_pick(hw, 0, target, &below) << hist_shift;
+            const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+            if (m < 0) set_status(FIM_ERR_INTERNAL);
+            if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
         }
     } else {
         for (int sd = warp; sd < nseeds; sd += nwarps) {
