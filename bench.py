@@ -79,6 +79,23 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """The largest x over the ranks of the process group (x itself without one): the job's
+    time is its slowest replica's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpix_per_s(px_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: every replica filters px_per_rank pixels; the job lasts as long
+    as its slowest replica."""
+    return px_per_rank * world / max_seconds / 1e6
+
+
 # ---------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------------
@@ -487,13 +504,9 @@ def run_native(args):
         raise RuntimeError(f"device status {fim.fim_status_string(status)}")
     step_ms = [s.elapsed_time(e) for s, e in step_events]
     launch_ms = [[s.elapsed_time(e) for s, e in ev] for ev in launch_events]
-    ms = sum(step_ms) / len(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(sum(step_ms) / len(step_ms), dist, dev)
     px_per_step = len(RADII) * H * W
-    value = px_per_step * world / (ms * 1e-3) / 1e6
+    value = job_mpix_per_s(px_per_step, world, ms * 1e-3)
 
     # --- end to end through the host-buffer API: H2D + filter + D2H every call -------------
     host_in = torch.from_numpy(img.view(np.int16)).pin_memory()
@@ -508,12 +521,8 @@ def run_native(args):
         for k in kernels:
             fim.fim_median_host(hp_in, hp_out, W, H, pitch, fim.FIM_U16, k, sh)
     barrier()
-    e2e_dt = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
-    e2e = {"value": px_per_step * world / e2e_dt / 1e6, "unit": "Mpix/s",
+    e2e_dt = reduce_max((time.perf_counter() - t0) / e2e_steps, dist, dev)
+    e2e = {"value": job_mpix_per_s(px_per_step, world, e2e_dt), "unit": "Mpix/s",
            "h2d_bytes_per_step": len(RADII) * H * W * 2, "d2h_bytes_per_step": len(RADII) * H * W * 2}
 
     # --- roofline of the tile kernel (all launches are the same kernel instantiation) -------
