@@ -272,11 +272,7 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
     const size_t om_bytes = align16((size_t)p->N * omb);
     const size_t ord_bytes = align16((size_t)SP * p->SH * 2);
     const size_t med_bytes = align16((size_t)Tx * Ty * 2);
-    // Large windows (measured: +1.7 % at r = 48, none at r = 32): the plain seed histograms are
-    // split over two warps per seed when the CTA has the warps. Not with a learned bracket,
-    // whose seeds take another path and whose staged weights need the shared memory.
-    p->seed_pairs = (!stage_model && p->n >= 5000 && p->nwarps >= 2 * p->RB * p->G) ? 1 : 0;
-    const size_t shist_bytes = (size_t)kSeedBins * std::min(p->nwarps, (1 + p->seed_pairs) * p->RB * p->G) * 4;
+    const size_t shist_bytes = (size_t)kSeedBins * std::min(p->nwarps, p->RB * p->G) * 4;
     const size_t solve_bytes = ord_bytes + med_bytes + shist_bytes;
     size_t tab = 0;
     auto take_tab = [&](int* field, size_t bytes) {

@@ -66,7 +66,6 @@ struct Plan {
     int vthreads;           // 2*Tx*RB: threads of the vertical sweep (the first ones of the CTA)
     int vmix;               // 1: the lanes of a vertical-sweep warp take their columns from all bands
     int scan_groups;        // 128-bit omnigram groups a vertical-sweep lane tests per scan step
-    int seed_pairs;         // 1: two warps share each plain seed window (large kernels)
     int S, SH;              // footprint bounding box (columns, rows)
     int SP;                 // row pitch (elements) of the ordinal image; SP/2 is odd
     int tiles_x, tiles_y;

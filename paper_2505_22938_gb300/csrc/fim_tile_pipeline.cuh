@@ -659,10 +659,9 @@ __device__ __forceinline__ void seed_features(const uint16_t* ord, int SP, const
 // loaded before they are handed to `f`, so the loads of a group overlap instead of each
 // waiting behind the previous group's shared-memory atomics.
 template <class Fn>
-__device__ __forceinline__ void window_walk(const int* spans, int nrows, const uint16_t* ctr, int SP, Fn&& f,
-                                            int first = -1, int step = 32) {
+__device__ __forceinline__ void window_walk(const int* spans, int nrows, const uint16_t* ctr, int SP, Fn&& f) {
     const int lane = threadIdx.x & 31;
-    for (int i = first < 0 ? lane : first; i < nrows; i += step) {
+    for (int i = lane; i < nrows; i += 32) {
         const int sp = spans[i];
         const int width = span_hi(sp) - span_lo(sp) + 1;
         const uint16_t* row = ctr + i * SP + span_lo(sp);
@@ -927,31 +926,6 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 }
             }
             G.sync();  // the next chunk reuses the activation buffers
-        }
-    } else if (P.seed_pairs && P.samples == nullptr && P.stats == nullptr) {
-        // large windows: two warps per seed window, each histogramming every other kernel row
-        // (the seed phase is a latency chain per warp); the first of the pair then adds the
-        // other's counts and refines
-        const int sd = warp >> 1, half = warp & 1;
-        uint32_t* hw = shist + warp * kSeedBins;
-        const int band = sd / P.G, g = sd % P.G;
-        const int s = g * GW + GW / 2, t = band * BH + BH / 2;
-        const int cu = s - xmin, cv = t - ymin;
-        if (sd < nseeds) {
-            for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
-            __syncwarp();
-            window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
-                        [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); }, 2 * lane + half, 64);
-        }
-        G.sync();
-        if (sd < nseeds && half == 0) {
-            for (int j = lane; j < kSeedBins; j += 32) hw[j] += hw[kSeedBins + j];
-            __syncwarp();
-            int below = 0;
-            const int pivot = hist_pick(hw, 0, target, &below) << hist_shift;
-            const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
-            if (m < 0) set_status(FIM_ERR_INTERNAL);
-            if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
         }
     } else {
         for (int sd = warp; sd < nseeds; sd += nwarps) {
