@@ -178,6 +178,9 @@ fim_status read_and_clear_batch_status();  // (fim_batch_kernel.cu) called by th
 fim_status launch_tile_kernel_k4(Plan& p, cudaStream_t stream);
 fim_status launch_tile_kernel_fixed_k4(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
 fim_status read_and_clear_k4_status();
+// (fim_tile_extras.cu) the kernels with the learned bracket, training rows and seed statistics
+fim_status launch_tile_kernel_extras(Plan& p, cudaStream_t stream);
+fim_status read_and_clear_extras_status();
 fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
 fim_status batch_prepare(int smem);
 fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);

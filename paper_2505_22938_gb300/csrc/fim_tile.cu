@@ -1,10 +1,11 @@
 // Single-image launches with 8 omnigram groups per scan step (the 1024-thread tiles of large
-// kernels) and the dispatch between the two sets of kernels.
+// kernels) and the dispatch between the sets of kernels.
 #include "fim_tile_launch.cuh"
 
 namespace fim {
 
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
+    if (p.model != nullptr || p.samples != nullptr || p.stats != nullptr) return launch_tile_kernel_extras(p, stream);
     return p.scan_groups == 4 ? launch_tile_kernel_k4(p, stream) : launch_tile_kernel_ks<8>(p, stream);
 }
 
@@ -19,7 +20,8 @@ fim_status read_and_clear_device_status(cudaStream_t stream) {
     const fim_status a = read_and_clear_unit_status();
     const fim_status b = read_and_clear_k4_status();
     const fim_status c = read_and_clear_batch_status();
-    return a != FIM_OK ? a : (b != FIM_OK ? b : c);
+    const fim_status d = read_and_clear_extras_status();
+    return a != FIM_OK ? a : (b != FIM_OK ? b : (c != FIM_OK ? c : d));
 }
 
 }  // namespace fim

@@ -10,7 +10,7 @@ namespace {
 
 // Persistent CTAs: each takes tiles from the queue counter in the scratch header until none are
 // left. The counter is zeroed on the stream before every launch.
-template <int DT, int SHAPE, int W, int OG, int KS>
+template <int DT, int SHAPE, int W, int OG, int KS, int XT>
 __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_constant__ Plan P) {
     __shared__ int s_tile;
     const int tid = threadIdx.x;
@@ -24,13 +24,13 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
         const int tile = s_tile;
         if (tile >= P.ntiles) break;
         stamp(P, tile, 0, G);
-        process_tile<DT, SHAPE, W, OG, KS>(P, P.tile0 + tile, gslice, G);
+        process_tile<DT, SHAPE, W, OG, KS, XT>(P, P.tile0 + tile, gslice, G);
     }
 }
 
-template <int DT, int SHAPE, int W, int OG, int KS>
+template <int DT, int SHAPE, int W, int OG, int KS, int XT>
 fim_status launch_typed(Plan& p, cudaStream_t stream) {
-    auto fn = tile_median_kernel<DT, SHAPE, W, OG, KS>;
+    auto fn = tile_median_kernel<DT, SHAPE, W, OG, KS, XT>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes) != cudaSuccess) {
         cudaGetLastError();
         return FIM_ERR_CUDA;
@@ -58,7 +58,7 @@ fim_status launch_typed(Plan& p, cudaStream_t stream) {
 // FIM_ERR_UNSUPPORTED when this launch would need more workspace than `capacity` bytes.
 template <int DT, int SHAPE, int W, int OG, int KS>
 fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
-    auto fn = tile_median_kernel<DT, SHAPE, W, OG, KS>;
+    auto fn = tile_median_kernel<DT, SHAPE, W, OG, KS, 0>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes) != cudaSuccess) {
         cudaGetLastError();
         return FIM_ERR_CUDA;
@@ -87,23 +87,27 @@ fim_status launch_w_fixed(Plan& p, unsigned char* scratch, size_t capacity, cuda
                         : launch_typed_fixed<DT, SHAPE, 0, 0, KS>(p, scratch, capacity, stream);
 }
 
-template <int DT, int SHAPE, int KS>
+template <int DT, int SHAPE, int KS, int XT>
 fim_status launch_w(Plan& p, cudaStream_t stream) {
-    if (p.wide) return launch_typed<DT, SHAPE, 1, 1, KS>(p, stream);
-    return p.loc_om < 0 ? launch_typed<DT, SHAPE, 0, 1, KS>(p, stream) : launch_typed<DT, SHAPE, 0, 0, KS>(p, stream);
+    if (p.wide) return launch_typed<DT, SHAPE, 1, 1, KS, XT>(p, stream);
+    return p.loc_om < 0 ? launch_typed<DT, SHAPE, 0, 1, KS, XT>(p, stream)
+                        : launch_typed<DT, SHAPE, 0, 0, KS, XT>(p, stream);
 }
 
 
-template <int KS>
+template <int KS, int XT = 0>
 fim_status launch_tile_kernel_ks(Plan& p, cudaStream_t stream) {
     const bool disk = p.shape == kShapeDisk;
     switch (p.dtype) {
         case FIM_U8:
-            return disk ? launch_w<FIM_U8, kShapeDisk, KS>(p, stream) : launch_w<FIM_U8, kShapeSpans, KS>(p, stream);
+            return disk ? launch_w<FIM_U8, kShapeDisk, KS, XT>(p, stream)
+                        : launch_w<FIM_U8, kShapeSpans, KS, XT>(p, stream);
         case FIM_U16:
-            return disk ? launch_w<FIM_U16, kShapeDisk, KS>(p, stream) : launch_w<FIM_U16, kShapeSpans, KS>(p, stream);
+            return disk ? launch_w<FIM_U16, kShapeDisk, KS, XT>(p, stream)
+                        : launch_w<FIM_U16, kShapeSpans, KS, XT>(p, stream);
         case FIM_F32:
-            return disk ? launch_w<FIM_F32, kShapeDisk, KS>(p, stream) : launch_w<FIM_F32, kShapeSpans, KS>(p, stream);
+            return disk ? launch_w<FIM_F32, kShapeDisk, KS, XT>(p, stream)
+                        : launch_w<FIM_F32, kShapeSpans, KS, XT>(p, stream);
     }
     return FIM_ERR_INVALID_ARG;
 }

@@ -725,7 +725,10 @@ __device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, 
 // KS: omnigram groups per scan step of the vertical sweep, fixed at compile time (4 or 8), or
 // 0 to follow the plan's scan_groups at run time (the batch kernel, which serves every plan:
 // one run-time loop keeps its 18 inlined pipelines small enough to compile quickly).
-template <int DT, int SHAPE, int W, int OG, int KS = 0>
+// XT: 1 compiles the extras — the learned bracket, training-row output and seed statistics —
+// which live in kernels of their own: at the 64-register cap of 1024-thread CTAs their code
+// changes how the compiler allocates the plain pipeline's registers, and the reverse.
+template <int DT, int SHAPE, int W, int OG, int KS = 0, int XT = 0>
 __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G) {
     extern __shared__ __align__(16) unsigned char smem_base[];
     unsigned char* const smem = smem_base + G.shift;  // this group's partition (tables excluded)
@@ -798,9 +801,11 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
     // (or, with a learned bracket, two exact counts at predicted ranks, then ballot refine)
     stamp(P, tile, 3, G);
-    const bool learned = P.model != nullptr;
+    const bool learned = XT && P.model != nullptr;
+    const bool sampling = XT && P.samples != nullptr;
+    const bool counting = XT && P.stats != nullptr;
     float* quant = reinterpret_cast<float*>(misc);  // the sort's scan scratch is free from here on
-    if (learned || P.samples != nullptr) {
+    if (learned || sampling) {
         if (warp == 0) {  // normalised value quantiles of the footprint: C at N (j + 1/2) / 32
             const int q = min(N - 1, (int)(((long long)N * (2 * lane + 1)) / (2 * kQuantiles)));
             const uint32_t e = om[q];
@@ -919,7 +924,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
                 if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
-                if (P.stats != nullptr && lane == 0) {
+                if (counting && lane == 0) {
                     atomicAdd(P.stats + 0, 1ull);
                     atomicAdd(P.stats + kind, 1ull);
                     atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
@@ -933,7 +938,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
             const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
             float fa = 0.f, fb = 0.f;
-            if (P.samples != nullptr) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+            if (sampling) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
             // one histogram per concurrently solved seed
             uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
             for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
@@ -946,7 +951,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
             if (m < 0) set_status(FIM_ERR_INTERNAL);
             if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
-            if (P.samples != nullptr) {  // training row: features and the exact median's place in [lof, hif]
+            if (sampling) {  // training row: features and the exact median's place in [lof, hif]
                 unsigned int row = 0;
                 if (lane == 0) row = atomicAdd(P.sample_count, 1u);
                 row = __shfl_sync(kFull, row, 0);
@@ -957,7 +962,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                     if (lane == 0) dst[kFeatures] = hif > lof ? (float)(max(m, 0) - lof) / (float)(hif - lof) : 0.5f;
                 }
             }
-            if (P.stats != nullptr && lane == 0) {
+            if (counting && lane == 0) {
                 atomicAdd(P.stats + 0, 1ull);
                 atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
             }
