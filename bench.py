@@ -176,7 +176,8 @@ def peak_alu_ops(clock_mhz: float) -> float:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("fim_tile_pipeline.cuh", "fim_tile_launch.cuh", "fim_tile.cu", "fim_tile_k4.cu", "fim_internal.h",
+    for name in ("fim_tile_pipeline.cuh", "fim_tile_launch.cuh", "fim_tile.cu", "fim_tile_k4.cu", "fim_tile_extras.cu",
+                 "fim_internal.h",
                  "fim_host.cu"):
         p = os.path.join(ROOT, "paper_2505_22938_gb300", "csrc", name)
         if os.path.exists(p):
