@@ -11,9 +11,9 @@ namespace {
 // memory, then each of its tile groups takes tiles of that job from the job's counter on its
 // own, with no CTA-wide barrier between tiles; when the job has no tiles left the CTA moves on.
 // The per-type pipelines are inlined into the kernel: behind a call boundary they spill.
-template <int DT, int SHAPE, int W, int OG>
+template <int DT, int SHAPE, int W, int OG, int KS = 0>
 __device__ __forceinline__ void batch_tile(const Plan* P, int tile, unsigned char* gslice, const Grp G) {
-    process_tile<DT, SHAPE, W, OG>(*P, tile, gslice, G);
+    process_tile<DT, SHAPE, W, OG, KS>(*P, tile, gslice, G);
 }
 
 __device__ __forceinline__ void dispatch_tile(const Plan* P, int tile, unsigned char* gslice, const Grp G) {
@@ -21,7 +21,8 @@ __device__ __forceinline__ void dispatch_tile(const Plan* P, int tile, unsigned 
     const bool disk = P->shape == kShapeDisk;
 #define FIM_CASE(DT)                                                                   \
     if (disk) {                                                                        \
-        if (cls == 0) batch_tile<DT, kShapeDisk, 0, 0>(P, tile, gslice, G);           \
+        if (cls == 0 && P->scan_groups == 8) batch_tile<DT, kShapeDisk, 0, 0, 8>(P, tile, gslice, G); \
+        else if (cls == 0) batch_tile<DT, kShapeDisk, 0, 0>(P, tile, gslice, G);      \
         else if (cls == 1) batch_tile<DT, kShapeDisk, 0, 1>(P, tile, gslice, G);      \
         else batch_tile<DT, kShapeDisk, 1, 1>(P, tile, gslice, G);                    \
     } else {                                                                           \
