@@ -11,9 +11,11 @@ Parts:
   * the filter itself (``fim_oracle.cpp``): clamp gather + ``std::nth_element``;
   * tile-footprint geometry used to pin the Fig. 10 counts.
 
-Every function states the passage it follows. Readings of the paper where it is silent
-or ambiguous are listed in the design doc of the repository (circle definition, even n,
-float ordering, border mode, polygon boundary).
+Every function states the passage it follows. Where the paper is silent or ambiguous this
+package reads it as follows: the circle is dx^2 + dy^2 <= r^2 (Eq. 3 on the lattice; the
+figures' counts use r^2 + r, available as a disk limit); an even tap count takes the lower
+median (rank (n - 1) // 2); floats are ordered by IEEE totalOrder (-0 < +0); borders clamp
+to the edge; polygon boundaries are inclusive with a 1e-9 tolerance.
 """
 from __future__ import annotations
 
