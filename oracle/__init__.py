@@ -15,7 +15,9 @@ Every function states the passage it follows. Where the paper is silent or ambig
 package reads it as follows: the circle is dx^2 + dy^2 <= r^2 (Eq. 3 on the lattice; the
 figures' counts use r^2 + r, available as a disk limit); an even tap count takes the lower
 median (rank (n - 1) // 2); floats are ordered by IEEE totalOrder (-0 < +0); borders clamp
-to the edge; polygon boundaries are inclusive with a 1e-9 tolerance.
+to the edge; polygon boundaries are inclusive with a 1e-9 tolerance; a spatially varying
+percentile (Fig. 14) is a float32 map with one percentile per output pixel, clamped to
+[0, 100] with NaN counted as 0, and rounded to a rank like a single percentile.
 """
 from __future__ import annotations
 
@@ -77,6 +79,11 @@ def _load():
                 ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+            lib.fim_oracle_filter_ranks.restype = ctypes.c_int
+            lib.fim_oracle_filter_ranks.argtypes = [
+                ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                ctypes.c_void_p, ctypes.c_int]
             lib.fim_oracle_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -159,6 +166,16 @@ def percentile_rank(n: int, pct: float) -> int:
     return int(math.floor(t + 0.5))
 
 
+def percentile_rank_map(n: int, pct: np.ndarray) -> np.ndarray:
+    """Per-pixel 0-based ranks for a map of percentiles (a spatially varying percentile,
+    Fig. 14): each value is clamped to [0, 100] (NaN counts as 0), widened to fp64, and
+    rounded as in percentile_rank: floor(p / 100 * (n - 1) + 1/2), evaluated in that order."""
+    p = np.asarray(pct, dtype=np.float32).astype(np.float64)
+    p = np.where(np.isnan(p), 0.0, np.clip(p, 0.0, 100.0))
+    t = p / 100.0 * float(n - 1)
+    return np.floor(t + 0.5).astype(np.int32)
+
+
 # --------------------------------------------------------------------------------------
 # The filter
 # --------------------------------------------------------------------------------------
@@ -177,6 +194,26 @@ def median_filter(img: np.ndarray, offsets: np.ndarray, rank: int | None = None,
     h, w = img.shape
     rc = _load().fim_oracle_filter(DTYPE_CODE[dt], img.ctypes.data, img.strides[0], out.ctypes.data,
                                    out.strides[0], w, h, dx.ctypes.data, dy.ctypes.data, n, k, nthreads)
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return out
+
+
+def rank_map_filter(img: np.ndarray, offsets: np.ndarray, ranks: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """Rank-order filter with its own 0-based rank at every pixel (ranks: same shape as img)."""
+    img = np.ascontiguousarray(img)
+    assert img.ndim == 2 and ranks.shape == img.shape
+    dt = dtype_name(img)
+    off = np.ascontiguousarray(offsets, dtype=np.int32)
+    n = off.shape[0]
+    dx = np.ascontiguousarray(off[:, 0])
+    dy = np.ascontiguousarray(off[:, 1])
+    rk = np.ascontiguousarray(ranks, dtype=np.int32)
+    out = np.empty_like(img)
+    h, w = img.shape
+    rc = _load().fim_oracle_filter_ranks(DTYPE_CODE[dt], img.ctypes.data, img.strides[0], out.ctypes.data,
+                                         out.strides[0], w, h, dx.ctypes.data, dy.ctypes.data, n,
+                                         rk.ctypes.data, nthreads)
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return out

@@ -72,6 +72,37 @@ void filter_all(const T* in, size_t in_pitch, T* out, size_t out_pitch, int w, i
     }
 }
 
+// The same definition with a rank of its own for every output pixel: ranks is w * h ints,
+// row-major, each in [0, n) (a spatially varying percentile, Fig. 14).
+template <typename T, typename Less>
+void filter_ranks(const T* in, size_t in_pitch, T* out, size_t out_pitch, int w, int h,
+                  const int* dx, const int* dy, int n, const int* ranks, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        std::vector<T> win((size_t)n);
+#pragma omp for schedule(dynamic, 1)
+        for (int y = 0; y < h; ++y) {
+            for (int x = 0; x < w; ++x) {
+                for (int t = 0; t < n; ++t) {
+                    int xx = clampi(x + dx[t], 0, w - 1);
+                    int yy = clampi(y + dy[t], 0, h - 1);
+                    const T* row = (const T*)((const char*)in + (size_t)yy * in_pitch);
+                    win[(size_t)t] = row[xx];
+                }
+                const int k = ranks[(size_t)y * w + x];
+                std::nth_element(win.begin(), win.begin() + k, win.end(), Less());
+                T* orow = (T*)((char*)out + (size_t)y * out_pitch);
+                orow[x] = win[(size_t)k];
+            }
+        }
+    }
+}
+
 template <typename T, typename Less>
 void filter_points(const T* in, size_t in_pitch, int w, int h, const int* px, const int* py,
                    long npts, const int* dx, const int* dy, int n, int rank, T* vals, int nthreads) {
@@ -110,6 +141,20 @@ int fim_oracle_filter(int dtype, const void* in, size_t in_pitch, void* out, siz
         case 0: filter_all<uint8_t, LessU8>((const uint8_t*)in, in_pitch, (uint8_t*)out, out_pitch, w, h, dx, dy, n, rank, nthreads); return 0;
         case 1: filter_all<uint16_t, LessU16>((const uint16_t*)in, in_pitch, (uint16_t*)out, out_pitch, w, h, dx, dy, n, rank, nthreads); return 0;
         case 2: filter_all<float, LessF32>((const float*)in, in_pitch, (float*)out, out_pitch, w, h, dx, dy, n, rank, nthreads); return 0;
+    }
+    return -1;
+}
+
+// Per-pixel ranks (w * h ints, row-major). Returns 0, or -1 on bad args (a rank outside [0, n)).
+int fim_oracle_filter_ranks(int dtype, const void* in, size_t in_pitch, void* out, size_t out_pitch,
+                            int w, int h, const int* dx, const int* dy, int n, const int* ranks, int nthreads) {
+    if (!in || !out || !ranks || w <= 0 || h <= 0 || n <= 0) return -1;
+    for (size_t i = 0; i < (size_t)w * h; ++i)
+        if (ranks[i] < 0 || ranks[i] >= n) return -1;
+    switch (dtype) {
+        case 0: filter_ranks<uint8_t, LessU8>((const uint8_t*)in, in_pitch, (uint8_t*)out, out_pitch, w, h, dx, dy, n, ranks, nthreads); return 0;
+        case 1: filter_ranks<uint16_t, LessU16>((const uint16_t*)in, in_pitch, (uint16_t*)out, out_pitch, w, h, dx, dy, n, ranks, nthreads); return 0;
+        case 2: filter_ranks<float, LessF32>((const float*)in, in_pitch, (float*)out, out_pitch, w, h, dx, dy, n, ranks, nthreads); return 0;
     }
     return -1;
 }

@@ -107,6 +107,77 @@ def test_points_match_full():
 
 
 # ----------------------------------------------------------------------------------------
+# 1b. spatially varying percentile (Fig. 14): a rank of its own at every pixel
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_rank_map_brute_force_tiny(dtype):
+    """Per-pixel ranks against a full sort of every window, pixel by pixel."""
+    rng = np.random.default_rng(17)
+    for name, off in kernel_zoo().items():
+        n = len(off)
+        for (h, w) in [(1, 1), (1, 7), (6, 1), (9, 13)]:
+            img = random_image(rng, dtype, h, w)
+            ranks = rng.integers(0, n, (h, w)).astype(np.int32)
+            got = oracle.rank_map_filter(img, off, ranks)
+            sorted_wins = {k: brute_force(img, off, k) for k in np.unique(ranks)}
+            for y in range(h):
+                for x in range(w):
+                    assert got[y, x] == sorted_wins[ranks[y, x]][y, x], (name, y, x)
+
+
+def test_rank_map_scipy_ramp():
+    """A left-to-right ramp from the 0th to the 100th percentile (the Fig. 14 setting) on an
+    asymmetric kernel: each pixel equals scipy's rank filter at that pixel's rank."""
+    nd = pytest.importorskip("scipy.ndimage")
+    img = datagen.image_for("u16", 21, 37, 45)
+    off = oracle.spans_offsets([0, -1, -2, -2, -1], [3, 2, 2, 1, 0], -2)
+    n = len(off)
+    pct = np.broadcast_to(np.linspace(0.0, 100.0, 45, dtype=np.float32), (37, 45))
+    ranks = oracle.percentile_rank_map(n, pct)
+    assert ranks[0, 0] == 0 and ranks[0, -1] == n - 1 and np.all(np.diff(ranks[0]) >= 0)
+    got = oracle.rank_map_filter(img, off, ranks)
+    for k in np.unique(ranks):
+        ref = nd.rank_filter(img, int(k), footprint=_footprint_mask(off), mode="nearest")
+        sel = ranks == k
+        assert np.array_equal(got[sel], ref[sel]), k
+    # a mirrored map (a plausible slip: x read right to left) disagrees
+    bad = oracle.rank_map_filter(img, off, ranks[:, ::-1].copy())
+    assert not np.array_equal(bad, got)
+
+
+def test_percentile_rank_map_closed_form():
+    """Ranks for n = 81 (n - 1 = 80, so rank = floor(0.8 p + 0.5)), clamping, NaN and infinities."""
+    pct = np.array([0.0, 50.0, 100.0, 12.5, 0.625, 0.6249, 99.375, 99.3749, -5.0, 150.0,
+                    np.nan, np.inf, -np.inf], dtype=np.float32)
+    exp = np.array([0, 40, 80, 10, 1, 0, 80, 79, 0, 80, 0, 80, 0], dtype=np.int32)
+    assert np.array_equal(oracle.percentile_rank_map(81, pct), exp)
+    # a constant map gives the single-percentile rank
+    for p in (0.0, 10.0, 33.3, 50.0, 90.0, 100.0):
+        for n in (1, 2, 49, 7845):
+            assert oracle.percentile_rank_map(n, np.float32([p]))[0] == oracle.percentile_rank(n, float(np.float32(p)))
+
+
+def test_constant_rank_map_is_the_percentile_filter():
+    rng = np.random.default_rng(4)
+    img = random_image(rng, "f32", 23, 29)
+    off = oracle.disk_offsets(3)
+    for k in (0, 7, len(off) - 1):
+        ranks = np.full(img.shape, k, np.int32)
+        assert np.array_equal(oracle.rank_map_filter(img, off, ranks), oracle.median_filter(img, off, rank=k))
+
+
+def test_rank_map_rejects_out_of_range_ranks():
+    img = np.zeros((4, 4), np.uint8)
+    off = oracle.disk_offsets(1)
+    for bad in (-1, len(off)):
+        ranks = np.zeros((4, 4), np.int32)
+        ranks[2, 3] = bad
+        with pytest.raises(ValueError):
+            oracle.rank_map_filter(img, off, ranks)
+
+
+# ----------------------------------------------------------------------------------------
 # 10. special case that reduces to a library routine: scipy.ndimage
 # ----------------------------------------------------------------------------------------
 
