@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=1024, help="rows of the image in the CPU oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batched comparison")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bracket comparison")
+    ap.add_argument("--no-multi", action="store_true", help="skip the several-percentiles comparison")
     ap.add_argument("--train-images", type=int, default=200)
     ap.add_argument("--profile-case", default=None, metavar="SIDE:R",
                     help="only run two launches on a SIDE x SIDE crop of the image at radius R (for ncu)")
@@ -298,6 +299,71 @@ def batched_section(fim, torch, reps: int = 3):
             "ms_batched_graph": ms_bat, "ms_sequential": ms_seq, "launches_batched": 1,
             "launches_sequential": len(jobs), "bit_exact_vs_sequential": bool(same), "status": status,
             "tiles": batch.info["total_tiles"], "autotune_s": round(tune_s, 2), "generate_s": round(gen_s, 2)}
+
+
+# ---------------------------------------------------------------------------------------------
+# quartiles from one ordinal transform vs three single-percentile launches (4096x4096 u16)
+# ---------------------------------------------------------------------------------------------
+
+def multi_percentile_section(fim, torch, img, reps: int = 3):
+    """25th/50th/75th percentiles of the 4096x4096 u16 image at disk r = 8, 32 and 48: one
+    fim_percentiles launch (one sort per tile) against three fim_percentile launches. Output
+    Mpix/s counts every output image; the outputs are compared bytewise. Also the spatially
+    varying percentile (fim_percentile_map, a 0-100 % left-to-right ramp as in Fig. 14) against
+    the plain median at the same radius."""
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    h, w = img.shape
+    pitch = img.stride(0) * img.element_size()
+    pcts = [25.0, 50.0, 75.0]
+    outs_m = [torch.empty_like(img) for _ in pcts]
+    outs_s = [torch.empty_like(img) for _ in pcts]
+    res = {}
+    same = True
+    ramp = torch.linspace(0.0, 100.0, w, device=img.device, dtype=torch.float32).expand(h, w).contiguous()
+    out_map = torch.empty_like(img)
+    for r in RADII:
+        k = fim.fim_create_kernel_circle(r)
+
+        def mapped():
+            fim.fim_percentile_map(img.data_ptr(), out_map.data_ptr(), ramp.data_ptr(), w * 4, w, h, pitch,
+                                   fim.FIM_U16, k, sh)
+
+        def median():
+            fim.fim_median(img.data_ptr(), out_map.data_ptr(), w, h, pitch, fim.FIM_U16, k, sh)
+
+        def multi():
+            fim.fim_percentiles(img.data_ptr(), [o.data_ptr() for o in outs_m], pcts, w, h, pitch, fim.FIM_U16, k,
+                                sh)
+
+        def single():
+            for pct, o in zip(pcts, outs_s):
+                fim.fim_percentile(img.data_ptr(), o.data_ptr(), w, h, pitch, fim.FIM_U16, k, pct, sh)
+
+        multi()
+        single()
+        mapped()
+        median()
+        times = {}
+        for name, fn in (("multi", multi), ("single", single), ("map", mapped), ("median", median)):
+            acc = 0.0
+            for _ in range(reps):
+                s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s_ev.record(stream)
+                fn()
+                e_ev.record(stream)
+                torch.cuda.synchronize()
+                acc += s_ev.elapsed_time(e_ev)
+            times[name] = acc / reps
+        same = same and all(torch.equal(a.view(torch.int16), b.view(torch.int16)) for a, b in zip(outs_m, outs_s))
+        mpix = len(pcts) * w * h / 1e6
+        res[f"r{r}"] = {"Mpix_s_one_launch": mpix / (times["multi"] * 1e-3),
+                        "Mpix_s_three_launches": mpix / (times["single"] * 1e-3),
+                        "speedup": times["single"] / times["multi"],
+                        "Mpix_s_percentile_map": w * h / 1e6 / (times["map"] * 1e-3),
+                        "Mpix_s_median": w * h / 1e6 / (times["median"] * 1e-3)}
+    return {"workload": "4096x4096 u16 photo-like, percentiles 25/50/75 and a 0-100 % ramp map, disk r = 8/32/48",
+            "per_radius": res, "bit_exact_vs_single": bool(same), "status": fim.fim_sync_status(sh)}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -563,6 +629,8 @@ def run_native(args):
     }
     if world == 1 and not args.no_batched:
         line["batched"] = batched_section(fim, torch)
+    if world == 1 and not args.no_multi:
+        line["percentiles"] = multi_percentile_section(fim, torch, src)
     if world == 1 and not args.no_learned:
         line["learned"] = learned_section(fim, torch, args.train_images)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

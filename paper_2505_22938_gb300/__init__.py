@@ -39,6 +39,10 @@ SIGNATURES = {
     "fim_median": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
     "fim_percentile": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_double,
                                   _c.c_int, _P]),
+    "fim_percentiles": (_c.c_int, [_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P,
+                                   _c.c_int, _P]),
+    "fim_percentile_map": (_c.c_int, [_P, _P, _P, _c.c_size_t, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P,
+                                      _c.c_int, _P]),
     "fim_median_host": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
     "fim_median_noalloc": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
     "fim_sync_status": (_c.c_int, [_P]),
@@ -194,6 +198,24 @@ def fim_percentile(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, 
                    percentile: float, stream: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
     _check(lib().fim_percentile(in_ptr, out_ptr, w, h, pitch_bytes, dtype, kernel.handle, float(percentile),
                                 border, stream or None), "fim_percentile")
+
+
+def fim_percentiles(in_ptr: int, out_ptrs, percentiles, w: int, h: int, pitch_bytes: int, dtype: int,
+                    kernel: Kernel, stream: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
+    """Several percentile filters of one image from one ordinal transform per tile."""
+    count = len(out_ptrs)
+    outs = (_c.c_void_p * max(count, 1))(*[_c.c_void_p(p) for p in out_ptrs])
+    pcts = (_c.c_double * max(len(percentiles), 1))(*[float(x) for x in percentiles])
+    _check(lib().fim_percentiles(in_ptr, outs, pcts, count, w, h, pitch_bytes, dtype, kernel.handle, border,
+                                 stream or None), "fim_percentiles")
+
+
+def fim_percentile_map(in_ptr: int, out_ptr: int, pct_ptr: int, pct_pitch_bytes: int, w: int, h: int,
+                       pitch_bytes: int, dtype: int, kernel: Kernel, stream: int = 0,
+                       border: int = FIM_BORDER_CLAMP) -> None:
+    """Rank-order filter with a percentile per output pixel (device float32 map)."""
+    _check(lib().fim_percentile_map(in_ptr, out_ptr, pct_ptr, pct_pitch_bytes, w, h, pitch_bytes, dtype,
+                                    kernel.handle, border, stream or None), "fim_percentile_map")
 
 
 def fim_median_host(in_ptr: int, out_ptr: int, w: int, h: int, pitch_bytes: int, dtype: int, kernel: Kernel,
@@ -420,6 +442,36 @@ def percentile(img, kernel: Kernel, pct: float, out=None, stream=None):
     pitch = img.stride(0) * img.element_size()
     h, w = img.shape
     fim_percentile(img.data_ptr(), out.data_ptr(), w, h, pitch, code, kernel, pct, _stream_handle(stream))
+    return out
+
+
+def percentiles(img, kernel: Kernel, pcts, stream=None):
+    """Returns one filtered image per percentile in `pcts` (at most 8), all from one launch."""
+    import torch
+    assert img.is_cuda and img.dim() == 2 and img.stride(1) == 1
+    code = _torch_dtype_code(img)
+    outs = [torch.empty_strided(img.shape, img.stride(), dtype=img.dtype, device=img.device) for _ in pcts]
+    pitch = img.stride(0) * img.element_size()
+    h, w = img.shape
+    fim_percentiles(img.data_ptr(), [o.data_ptr() for o in outs], list(pcts), w, h, pitch, code, kernel,
+                    _stream_handle(stream))
+    return outs
+
+
+def percentile_map(img, kernel: Kernel, pct, out=None, stream=None):
+    """Filters a 2-D CUDA tensor with a percentile per pixel: pct is a float32 CUDA tensor of
+    the image's shape (values in [0, 100])."""
+    import torch
+    assert img.is_cuda and img.dim() == 2 and img.stride(1) == 1
+    assert pct.is_cuda and pct.dtype == torch.float32 and pct.shape == img.shape and pct.stride(1) == 1
+    code = _torch_dtype_code(img)
+    if out is None:
+        out = torch.empty_strided(img.shape, img.stride(), dtype=img.dtype, device=img.device)
+    assert out.shape == img.shape and out.dtype == img.dtype and out.stride(0) == img.stride(0)
+    pitch = img.stride(0) * img.element_size()
+    h, w = img.shape
+    fim_percentile_map(img.data_ptr(), out.data_ptr(), pct.data_ptr(), pct.stride(0) * 4, w, h, pitch, code,
+                       kernel, _stream_handle(stream))
     return out
 
 

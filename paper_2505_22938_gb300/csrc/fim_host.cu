@@ -203,6 +203,8 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->ncols = k->xmax - k->xmin + 1;
     p->n = k->n;
     p->rank = rank;
+    p->nranks = 1;
+    p->ranks[0] = rank;
     // Small kernels: a warp's 32 chains drawn from every band even out the per-warp work of the
     // vertical sweep (scan lengths follow the image content of a band); large kernels prefer the
     // shorter per-step divergence of 32 adjacent columns of one band (measured on the 4096^2
@@ -659,6 +661,89 @@ fim_status fim_percentile(const void* in, void* out, int w, int h, size_t pitch_
     const int rank = (int)floor(percentile / 100.0 * (k->n - 1) + 0.5);
     return filter_rank(in, out, w, h, pitch_bytes, dtype, k, std::min(std::max(rank, 0), k->n - 1),
                        (cudaStream_t)stream);
+}
+
+fim_status fim_percentiles(const void* in, void* const* outs, const double* percentiles, int count, int w, int h,
+                           size_t pitch_bytes, fim_dtype dtype, const fim_kernel* k, fim_border border,
+                           void* stream) {
+    if (!outs || !percentiles || count < 1 || count > kMaxRanks) return FIM_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        fim_status s = check_image_args(in, outs[i], w, h, pitch_bytes, dtype, k, border);
+        if (s != FIM_OK) return s;
+        if (!(percentiles[i] >= 0.0 && percentiles[i] <= 100.0)) return FIM_ERR_INVALID_ARG;
+    }
+    static thread_local int smem_limit = -1;
+    if (smem_limit < 0) smem_limit = device_smem_limit();
+    if (smem_limit <= 0) return FIM_ERR_CUDA;
+    TileShape ts;
+    fim_status s = choose_tile(k, dtype, smem_limit, &ts);
+    if (s != FIM_OK) return s;
+    int ranks[kMaxRanks];
+    for (int i = 0; i < count; ++i)
+        ranks[i] = std::min(std::max((int)floor(percentiles[i] / 100.0 * (k->n - 1) + 0.5), 0), k->n - 1);
+    Plan* p = new (std::nothrow) Plan;
+    if (!p) return FIM_ERR_OOM;
+    s = make_plan(k, dtype, ranks[0], w, h, ts, smem_limit, p);
+    if (s == FIM_OK) {
+        p->in = in;
+        p->out = outs[0];
+        p->pitch = (long long)pitch_bytes;
+        p->nranks = count;
+        for (int i = 0; i < count; ++i) {
+            p->ranks[i] = ranks[i];
+            p->outs[i] = outs[i];
+        }
+        get_phase_clock_buffer(&p->phase_clock, &p->phase_tiles);
+        s = launch_tile_kernel(*p, (cudaStream_t)stream);
+    }
+    delete p;
+    return s;
+}
+
+fim_status fim_percentile_map(const void* in, void* out, const float* percentiles, size_t pct_pitch_bytes, int w,
+                              int h, size_t pitch_bytes, fim_dtype dtype, const fim_kernel* k, fim_border border,
+                              void* stream) {
+    fim_status s = check_image_args(in, out, w, h, pitch_bytes, dtype, k, border);
+    if (s != FIM_OK) return s;
+    if (!percentiles || pct_pitch_bytes < (size_t)w * sizeof(float) || pct_pitch_bytes % sizeof(float) != 0)
+        return FIM_ERR_INVALID_ARG;
+    const size_t map_span = pct_pitch_bytes * (size_t)(h - 1) + (size_t)w * sizeof(float);
+    const size_t out_span = pitch_bytes * (size_t)(h - 1) + (size_t)w * (size_t)elem_size(dtype);
+    const char* m0 = reinterpret_cast<const char*>(percentiles);
+    const char* o0 = static_cast<const char*>(out);
+    if (m0 < o0 + out_span && o0 < m0 + map_span) return FIM_ERR_INVALID_ARG;  // the map must outlive the writes
+    static thread_local int smem_limit = -1;
+    if (smem_limit < 0) smem_limit = device_smem_limit();
+    if (smem_limit <= 0) return FIM_ERR_CUDA;
+    TileShape ts;
+    s = choose_tile(k, dtype, smem_limit, &ts);
+    if (s != FIM_OK) return s;
+    Plan* p = new (std::nothrow) Plan;
+    if (!p) return FIM_ERR_OOM;
+    s = make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, smem_limit, p);
+    if (s == FIM_OK) {
+        p->in = in;
+        p->out = out;
+        p->pitch = (long long)pitch_bytes;
+        // the rank image lives in stream-ordered memory: allocated, filled, read by the filter and
+        // released in stream order, so the call stays asynchronous
+        const cudaStream_t st = (cudaStream_t)stream;
+        int* ranks = nullptr;
+        if (cudaMallocAsync(reinterpret_cast<void**>(&ranks), (size_t)w * (size_t)h * sizeof(int), st) != cudaSuccess) {
+            cudaGetLastError();
+            s = FIM_ERR_OOM;
+        } else {
+            s = launch_percentile_ranks(percentiles, (long long)pct_pitch_bytes, w, h, k->n, ranks, st);
+            if (s == FIM_OK) {
+                p->rank_map = ranks;
+                get_phase_clock_buffer(&p->phase_clock, &p->phase_tiles);
+                s = launch_tile_kernel(*p, st);
+            }
+            if (cudaFreeAsync(ranks, st) != cudaSuccess && s == FIM_OK) s = FIM_ERR_CUDA;
+        }
+    }
+    delete p;
+    return s;
 }
 
 fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, size_t pitch_bytes,

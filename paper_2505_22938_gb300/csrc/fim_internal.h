@@ -20,6 +20,9 @@ constexpr int kSeedBins = 256;    // coarse histogram bins of a seed solve
 
 enum Shape : int { kShapeDisk = 0, kShapeSpans = 1 };
 
+// Target ranks one launch can serve from one ordinal transform (fim_percentiles).
+constexpr int kMaxRanks = 8;
+
 // Rank-bracket MLP: kFeatures inputs -> kHidden -> kHidden -> 2 (predicted rank, log scale).
 constexpr int kQuantiles = 32;   // footprint value quantiles
 constexpr int kNeigh = 9;        // 3x3 neighbourhood ranks of the window centre
@@ -75,6 +78,9 @@ struct Plan {
     int xmin, xmax, ymin, ymax, nrows, ncols;
     int n;                  // taps
     int rank;               // target 0-based rank ((n-1)/2 for the median)
+    int nranks;             // extras kernels: target ranks served by one ordinal transform (1..kMaxRanks)
+    int ranks[kMaxRanks];   //   their ranks; entry 0 is taken from `rank`
+    void* outs[kMaxRanks];  //   and their outputs (same pitch as the input); entry 0 is taken from `out`
     // footprint
     int N;                  // pixels in the rounded-rectangle footprint
     int cx0, cy0;           // omnigram coordinates are stored as (u - cx0, v - cy0), int8 each
@@ -89,6 +95,8 @@ struct Plan {
     float* samples;                   // training rows: kFeatures features + 1 label each
     unsigned int* sample_count;       // rows written so far (device counter)
     int sample_cap;                   // capacity of samples in rows
+    // spatially varying percentile (extras kernels; null = every pixel takes `rank`)
+    const int* rank_map;              // one target rank per output pixel, w x h, dense rows
     unsigned long long* phase_clock;  // optional: 8 clock64() stamps per tile (diagnostics)
     int phase_tiles;                  // capacity of phase_clock in tiles
     // Array placement. A location >= 0 is a byte offset into dynamic shared memory; a location
@@ -181,6 +189,10 @@ fim_status read_and_clear_k4_status();
 // (fim_tile_extras.cu) the kernels with the learned bracket, training rows and seed statistics
 fim_status launch_tile_kernel_extras(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_extras_status();
+// Per-pixel target ranks of a percentile map (w x h floats, pitch in bytes) into `ranks`
+// (w x h ints, dense rows), on `stream`.
+fim_status launch_percentile_ranks(const float* pct, long long pct_pitch, int w, int h, int n, int* ranks,
+                                   cudaStream_t stream);
 fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
 fim_status batch_prepare(int smem);
 fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);

@@ -5,7 +5,8 @@
 namespace fim {
 
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
-    if (p.model != nullptr || p.samples != nullptr || p.stats != nullptr) return launch_tile_kernel_extras(p, stream);
+    if (p.model != nullptr || p.samples != nullptr || p.stats != nullptr || p.nranks > 1 || p.rank_map != nullptr)
+        return launch_tile_kernel_extras(p, stream);
     return p.scan_groups == 4 ? launch_tile_kernel_k4(p, stream) : launch_tile_kernel_ks<8>(p, stream);
 }
 

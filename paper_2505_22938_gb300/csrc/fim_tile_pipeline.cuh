@@ -686,7 +686,14 @@ __device__ __forceinline__ void window_walk(const int* spans, int nrows, const u
     }
 }
 
-// Seed histogram (kSeedBins bins of one warp): the bin holding window-rank `target` when// Seed histogram (kSeedBins bins of one warp): the bin holding window-rank `target` when
+// Target rank of output pixel (gx, gy) under a percentile map (Fig. 14), from the rank image
+// the host computed before the launch. Pixels beyond the image (the ragged edge of a tile) take
+// the nearest pixel's rank; their results are never stored.
+__device__ __forceinline__ int map_rank(const Plan& P, int gx, int gy) {
+    return __ldg(P.rank_map + (long long)min(gy, P.h - 1) * P.w + min(gx, P.w - 1));
+}
+
+// Seed histogram (kSeedBins bins of one warp): the bin holding window-rank `target` when
 // `base` window members lie below bin 0. Returns the bin and, in *below, the members below it.
 __device__ __forceinline__ int hist_pick(const uint32_t* hw, int base, int target, int* below) {
     const int lane = threadIdx.x & 31;
@@ -792,284 +799,299 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         member.ymin = P.ymin;
         member.nrows = P.nrows;
     }
-    const int target = P.rank;
-    const int BH = TY / P.RB;      // band height
-    const int GW = TX / P.G;       // seed spacing within a seed row
-    // feasible median ranks of any window of this tile (Fig. 10): [lof, hif]
-    const int lof = target, hif = N - P.n + target;
+    // Extras kernels may take several target ranks (percentiles) of one window size: the
+    // ordinal transform and the ordinal image above are built once and serve them all.
+    const int nr = XT ? P.nranks : 1;
+    // With a percentile map every output pixel has its own target rank. A slide's pivot is the
+    // previous window's result, which has exactly that window's target below it, so the count
+    // at the pivot after the slide is the previous target plus the change.
+    const bool mapped = XT && P.rank_map != nullptr;
+    for (int q = 0; q < nr; ++q) {
+        const int target = q == 0 ? P.rank : P.ranks[q];
+        const int BH = TY / P.RB;      // band height
+        const int GW = TX / P.G;       // seed spacing within a seed row
+        // feasible median ranks of any window of this tile (Fig. 10): [lof, hif]
+        const int lof = target, hif = N - P.n + target;
 
-    // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
-    // (or, with a learned bracket, two exact counts at predicted ranks, then ballot refine)
-    stamp(P, tile, 3, G);
-    const bool learned = XT && P.model != nullptr;
-    const bool sampling = XT && P.samples != nullptr;
-    const bool counting = XT && P.stats != nullptr;
-    float* quant = reinterpret_cast<float*>(misc);  // the sort's scan scratch is free from here on
-    if (learned || sampling) {
-        if (warp == 0) {  // normalised value quantiles of the footprint: C at N (j + 1/2) / 32
-            const int q = min(N - 1, (int)(((long long)N * (2 * lane + 1)) / (2 * kQuantiles)));
-            const uint32_t e = om[q];
-            const float v = (float)load_px<DT>(Img(P), gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
-            const float mid = __shfl_sync(kFull, v, kQuantiles / 2);
-            const float spread = __shfl_sync(kFull, v, 7 * kQuantiles / 8) - __shfl_sync(kFull, v, kQuantiles / 8);
-            const float z = (v - mid) / (spread > 0.f ? spread : 1.f);
-            quant[lane] = fminf(fmaxf(z, -8.f), 8.f);
+        // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
+        // (or, with a learned bracket, two exact counts at predicted ranks, then ballot refine)
+        stamp(P, tile, 3, G);
+        const bool learned = XT && P.model != nullptr;
+        const bool sampling = XT && P.samples != nullptr;
+        const bool counting = XT && P.stats != nullptr;
+        float* quant = reinterpret_cast<float*>(misc);  // the sort's scan scratch is free from here on
+        if (learned || sampling) {
+            if (warp == 0) {  // normalised value quantiles of the footprint: C at N (j + 1/2) / 32
+                const int q = min(N - 1, (int)(((long long)N * (2 * lane + 1)) / (2 * kQuantiles)));
+                const uint32_t e = om[q];
+                const float v = (float)load_px<DT>(Img(P), gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
+                const float mid = __shfl_sync(kFull, v, kQuantiles / 2);
+                const float spread = __shfl_sync(kFull, v, 7 * kQuantiles / 8) - __shfl_sync(kFull, v, kQuantiles / 8);
+                const float z = (v - mid) / (spread > 0.f ? spread : 1.f);
+                quant[lane] = fminf(fmaxf(z, -8.f), 8.f);
+            }
+            G.sync();
         }
-        G.sync();
-    }
-    const int nseeds = P.RB * P.G;
-    static_assert(kHidden + kNeigh + 2 * kHidden <= kSeedBins, "MLP activations fit a seed histogram per seed");
-    if (learned) {
-        // Learned bracket (extension): the bracket MLP runs block-wide over a chunk of seeds
-        // (thread per (seed, hidden unit), activations in the seed-histogram buffers), then one
-        // warp per seed counts its window at the bracket ends, histograms the ranks inside the
-        // bracket finely, and scans Omega from the fine bin of the target (or, on a miss, from
-        // the bracket end the target lies beyond).
-        const uint16_t* wts =
-            P.off_model >= 0 ? reinterpret_cast<const uint16_t*>(smem_base + P.off_model) : P.model;
-        const int chunk_max = min(nwarps, nseeds);
-        // activations: 64 + chunk * (9 + 64 + 64) floats, within the chunk * 1 KiB of histograms
-        float* hbase = reinterpret_cast<float*>(shist);  // layer-1 pre-activation of the quantiles
-        float* xs = hbase + kHidden;                      // [chunk][kNeigh]
-        float* h1 = xs + chunk_max * kNeigh;              // [chunk][kHidden]
-        float* h2 = h1 + chunk_max * kHidden;             // [chunk][kHidden]
-        for (int j = tid; j < kHidden; j += nthreads) {
-            float h = bf16_to_f32(wts[kOffB1 + j]);
-            for (int i = 0; i < kQuantiles; ++i) h = fmaf(quant[i], bf16_to_f32(wts[kOffW1 + i * kHidden + j]), h);
-            hbase[j] = h;
-        }
-        for (int c0 = 0; c0 < nseeds; c0 += chunk_max) {
-            const int chunk = min(chunk_max, nseeds - c0);
-            if (warp < chunk) {
-                const int sd = c0 + warp;
-                const int band = sd / P.G, g = sd % P.G;
-                const int cu = g * GW + GW / 2 - xmin, cv = band * BH + BH / 2 - ymin;
-                float fa, fb;
-                seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
-                if (lane < kNeigh) xs[warp * kNeigh + lane] = fb;
+        const int nseeds = P.RB * P.G;
+        static_assert(kHidden + kNeigh + 2 * kHidden <= kSeedBins, "MLP activations fit a seed histogram per seed");
+        if (learned) {
+            // Learned bracket (extension): the bracket MLP runs block-wide over a chunk of seeds
+            // (thread per (seed, hidden unit), activations in the seed-histogram buffers), then one
+            // warp per seed counts its window at the bracket ends, histograms the ranks inside the
+            // bracket finely, and scans Omega from the fine bin of the target (or, on a miss, from
+            // the bracket end the target lies beyond).
+            const uint16_t* wts =
+                P.off_model >= 0 ? reinterpret_cast<const uint16_t*>(smem_base + P.off_model) : P.model;
+            const int chunk_max = min(nwarps, nseeds);
+            // activations: 64 + chunk * (9 + 64 + 64) floats, within the chunk * 1 KiB of histograms
+            float* hbase = reinterpret_cast<float*>(shist);  // layer-1 pre-activation of the quantiles
+            float* xs = hbase + kHidden;                      // [chunk][kNeigh]
+            float* h1 = xs + chunk_max * kNeigh;              // [chunk][kHidden]
+            float* h2 = h1 + chunk_max * kHidden;             // [chunk][kHidden]
+            for (int j = tid; j < kHidden; j += nthreads) {
+                float h = bf16_to_f32(wts[kOffB1 + j]);
+                for (int i = 0; i < kQuantiles; ++i) h = fmaf(quant[i], bf16_to_f32(wts[kOffW1 + i * kHidden + j]), h);
+                hbase[j] = h;
             }
-            G.sync();
-            for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
-                const int sl = idx / kHidden, j = idx % kHidden;
-                float h = hbase[j];
-#pragma unroll
-                for (int i = 0; i < kNeigh; ++i)
-                    h = fmaf(xs[sl * kNeigh + i], bf16_to_f32(wts[kOffW1 + (kQuantiles + i) * kHidden + j]), h);
-                h1[idx] = fmaxf(h, 0.f);
-            }
-            G.sync();
-            for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
-                const int sl = idx / kHidden, j = idx % kHidden;
-                float h = bf16_to_f32(wts[kOffB2 + j]);
-#pragma unroll 8
-                for (int k = 0; k < kHidden; ++k) h = fmaf(h1[sl * kHidden + k], bf16_to_f32(wts[kOffW2 + k * kHidden + j]), h);
-                h2[idx] = fmaxf(h, 0.f);
-            }
-            G.sync();
-            int lo = 0, hi = 0;
-            if (warp < chunk) {  // output layer: lanes hold hidden units lane and lane + 32
-                const float x0 = h2[warp * kHidden + lane], x1 = h2[warp * kHidden + lane + 32];
-                float o0 = bf16_to_f32(wts[kOffW3 + lane * 2]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2]) * x1;
-                float o1 = bf16_to_f32(wts[kOffW3 + lane * 2 + 1]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2 + 1]) * x1;
-                for (int o = 16; o > 0; o >>= 1) {
-                    o0 += __shfl_xor_sync(kFull, o0, o);
-                    o1 += __shfl_xor_sync(kFull, o1, o);
+            for (int c0 = 0; c0 < nseeds; c0 += chunk_max) {
+                const int chunk = min(chunk_max, nseeds - c0);
+                if (warp < chunk) {
+                    const int sd = c0 + warp;
+                    const int band = sd / P.G, g = sd % P.G;
+                    const int cu = g * GW + GW / 2 - xmin, cv = band * BH + BH / 2 - ymin;
+                    float fa, fb;
+                    seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+                    if (lane < kNeigh) xs[warp * kNeigh + lane] = fb;
                 }
-                o0 += bf16_to_f32(wts[kOffB3]);
-                o1 += bf16_to_f32(wts[kOffB3 + 1]);
-                const float sig = __expf(fminf(fmaxf(o1, -8.f), 2.f)) * P.bracket_z;
-                const float span = (float)(hif - lof);
-                lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
-                hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
+                G.sync();
+                for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
+                    const int sl = idx / kHidden, j = idx % kHidden;
+                    float h = hbase[j];
+    #pragma unroll
+                    for (int i = 0; i < kNeigh; ++i)
+                        h = fmaf(xs[sl * kNeigh + i], bf16_to_f32(wts[kOffW1 + (kQuantiles + i) * kHidden + j]), h);
+                    h1[idx] = fmaxf(h, 0.f);
+                }
+                G.sync();
+                for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
+                    const int sl = idx / kHidden, j = idx % kHidden;
+                    float h = bf16_to_f32(wts[kOffB2 + j]);
+    #pragma unroll 8
+                    for (int k = 0; k < kHidden; ++k) h = fmaf(h1[sl * kHidden + k], bf16_to_f32(wts[kOffW2 + k * kHidden + j]), h);
+                    h2[idx] = fmaxf(h, 0.f);
+                }
+                G.sync();
+                int lo = 0, hi = 0;
+                if (warp < chunk) {  // output layer: lanes hold hidden units lane and lane + 32
+                    const float x0 = h2[warp * kHidden + lane], x1 = h2[warp * kHidden + lane + 32];
+                    float o0 = bf16_to_f32(wts[kOffW3 + lane * 2]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2]) * x1;
+                    float o1 = bf16_to_f32(wts[kOffW3 + lane * 2 + 1]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2 + 1]) * x1;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        o0 += __shfl_xor_sync(kFull, o0, o);
+                        o1 += __shfl_xor_sync(kFull, o1, o);
+                    }
+                    o0 += bf16_to_f32(wts[kOffB3]);
+                    o1 += bf16_to_f32(wts[kOffB3 + 1]);
+                    const float sig = __expf(fminf(fmaxf(o1, -8.f), 2.f)) * P.bracket_z;
+                    const float span = (float)(hif - lof);
+                    lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
+                    hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
+                }
+                G.sync();  // the histograms below overwrite the activations
+                if (warp < chunk) {
+                    const int sd = c0 + warp;
+                    const int band = sd / P.G, g = sd % P.G;
+                    const int s = g * GW + GW / 2, t = band * BH + BH / 2;
+                    const int cu = s - xmin, cv = t - ymin;
+                    // One pass counts the window below lo and at or below hi and histograms the ranks
+                    // inside [lo, hi] in kFineBins fine bins. Every pixel makes one atomic: pixels
+                    // outside the bracket add to a lane-private spare word (its own bank), so the
+                    // bracket's few pixels are the only ones that can collide.
+                    constexpr int kFineBins = kSeedBins - 32;
+                    int hb = 0;
+                    while (((hi - lo) >> hb) >= kFineBins) ++hb;
+                    uint32_t* hw = shist + warp * kSeedBins;
+                    for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+                    __syncwarp();
+                    int clo = 0, chi = 0;
+                    window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
+                        clo += r < lo;
+                        chi += r <= hi;
+                        const bool in = (unsigned)(r - lo) <= (unsigned)(hi - lo);
+                        atomicAdd(&hw[in ? (r - lo) >> hb : kFineBins + lane], 1u);
+                    });
+                    clo = __reduce_add_sync(kFull, clo);
+                    chi = __reduce_add_sync(kFull, chi);
+                    __syncwarp();
+                    int pivot, below, kind;
+                    if (target < clo) {         // below the bracket: walk down from lo
+                        pivot = lo;
+                        below = clo;
+                        kind = 2;
+                    } else if (target >= chi) { // above the bracket: walk up from hi + 1
+                        pivot = hi + 1;
+                        below = chi;
+                        kind = 3;
+                    } else {                    // inside: the fine bin holding the target (the spare
+                        kind = 1;               // words come after every fine bin, so are not reached)
+                        pivot = lo + (hist_pick(hw, clo, target, &below) << hb);
+                    }
+                    const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+                    if (m < 0) set_status(FIM_ERR_INTERNAL);
+                    if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+                    if (counting && lane == 0) {
+                        atomicAdd(P.stats + 0, 1ull);
+                        atomicAdd(P.stats + kind, 1ull);
+                        atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
+                    }
+                }
+                G.sync();  // the next chunk reuses the activation buffers
             }
-            G.sync();  // the histograms below overwrite the activations
-            if (warp < chunk) {
-                const int sd = c0 + warp;
+        } else {
+            for (int sd = warp; sd < nseeds; sd += nwarps) {
                 const int band = sd / P.G, g = sd % P.G;
-                const int s = g * GW + GW / 2, t = band * BH + BH / 2;
-                const int cu = s - xmin, cv = t - ymin;
-                // One pass counts the window below lo and at or below hi and histograms the ranks
-                // inside [lo, hi] in kFineBins fine bins. Every pixel makes one atomic: pixels
-                // outside the bracket add to a lane-private spare word (its own bank), so the
-                // bracket's few pixels are the only ones that can collide.
-                constexpr int kFineBins = kSeedBins - 32;
-                int hb = 0;
-                while (((hi - lo) >> hb) >= kFineBins) ++hb;
-                uint32_t* hw = shist + warp * kSeedBins;
+                const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
+                const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
+                float fa = 0.f, fb = 0.f;
+                if (sampling) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+                // one histogram per concurrently solved seed
+                uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
                 for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
                 __syncwarp();
-                int clo = 0, chi = 0;
-                window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
-                    clo += r < lo;
-                    chi += r <= hi;
-                    const bool in = (unsigned)(r - lo) <= (unsigned)(hi - lo);
-                    atomicAdd(&hw[in ? (r - lo) >> hb : kFineBins + lane], 1u);
-                });
-                clo = __reduce_add_sync(kFull, clo);
-                chi = __reduce_add_sync(kFull, chi);
+                window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
+                            [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
                 __syncwarp();
-                int pivot, below, kind;
-                if (target < clo) {         // below the bracket: walk down from lo
-                    pivot = lo;
-                    below = clo;
-                    kind = 2;
-                } else if (target >= chi) { // above the bracket: walk up from hi + 1
-                    pivot = hi + 1;
-                    below = chi;
-                    kind = 3;
-                } else {                    // inside: the fine bin holding the target (the spare
-                    kind = 1;               // words come after every fine bin, so are not reached)
-                    pivot = lo + (hist_pick(hw, clo, target, &below) << hb);
-                }
-                const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+                int below = 0;
+                const int ts = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
+                const int pivot = hist_pick(hw, 0, ts, &below) << hist_shift;
+                const int m = ballot_select(om, N, pivot, below, ts, cu - cx0, cv - cy0, member);
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
                 if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+                if (sampling) {  // training row: features and the exact median's place in [lof, hif]
+                    unsigned int row = 0;
+                    if (lane == 0) row = atomicAdd(P.sample_count, 1u);
+                    row = __shfl_sync(kFull, row, 0);
+                    if ((int)row < P.sample_cap) {
+                        float* dst = P.samples + (size_t)row * (kFeatures + 1);
+                        dst[lane] = fa;
+                        if (lane < kNeigh) dst[kQuantiles + lane] = fb;
+                        if (lane == 0) dst[kFeatures] = hif > lof ? (float)(max(m, 0) - lof) / (float)(hif - lof) : 0.5f;
+                    }
+                }
                 if (counting && lane == 0) {
                     atomicAdd(P.stats + 0, 1ull);
-                    atomicAdd(P.stats + kind, 1ull);
                     atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
                 }
+                __syncwarp();
             }
-            G.sync();  // the next chunk reuses the activation buffers
         }
-    } else {
-        for (int sd = warp; sd < nseeds; sd += nwarps) {
+        G.sync();
+
+        // ---- 4. seed rows: horizontal slides, lanes split the kernel rows ----------------------
+        stamp(P, tile, 4, G);
+        for (int job = warp; job < 2 * P.RB * P.G; job += nwarps) {
+            const int sd = job >> 1, right = job & 1;
             const int band = sd / P.G, g = sd % P.G;
-            const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
-            const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
-            float fa = 0.f, fb = 0.f;
-            if (sampling) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
-            // one histogram per concurrently solved seed
-            uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
-            for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
-            __syncwarp();
-            window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
-                        [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
-            __syncwarp();
-            int below = 0;
-            const int pivot = hist_pick(hw, 0, target, &below) << hist_shift;
-            const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
-            if (m < 0) set_status(FIM_ERR_INTERNAL);
-            if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
-            if (sampling) {  // training row: features and the exact median's place in [lof, hif]
-                unsigned int row = 0;
-                if (lane == 0) row = atomicAdd(P.sample_count, 1u);
-                row = __shfl_sync(kFull, row, 0);
-                if ((int)row < P.sample_cap) {
-                    float* dst = P.samples + (size_t)row * (kFeatures + 1);
-                    dst[lane] = fa;
-                    if (lane < kNeigh) dst[kQuantiles + lane] = fb;
-                    if (lane == 0) dst[kFeatures] = hif > lof ? (float)(max(m, 0) - lof) / (float)(hif - lof) : 0.5f;
+            int s = g * GW + GW / 2;
+            const int t = band * BH + BH / 2;
+            const int steps = right ? (GW - GW / 2 - 1) : (GW / 2);
+            int cu = s - xmin;
+            const int cv = t - ymin;
+            int p = med[t * TX + s];
+            constexpr int kRowsPerLane = (kMaxExtent + 31) / 32;
+            int eo[kRowsPerLane], lo[kRowsPerLane];  // this lane's rows: entering / leaving offsets
+    #pragma unroll
+            for (int q = 0; q < kRowsPerLane; ++q) {
+                const int i = lane + 32 * q;
+                eo[q] = lo[q] = 0;  // rows beyond the kernel compare the centre with itself: no change
+                if (i < P.nrows) {
+                    const int2 o = htab[i];
+                    eo[q] = right ? o.y : o.x - 1;
+                    lo[q] = right ? o.x : o.y - 1;
                 }
             }
-            if (counting && lane == 0) {
-                atomicAdd(P.stats + 0, 1ull);
-                atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
-            }
-            __syncwarp();
-        }
-    }
-    G.sync();
-
-    // ---- 4. seed rows: horizontal slides, lanes split the kernel rows ----------------------
-    stamp(P, tile, 4, G);
-    for (int job = warp; job < 2 * P.RB * P.G; job += nwarps) {
-        const int sd = job >> 1, right = job & 1;
-        const int band = sd / P.G, g = sd % P.G;
-        int s = g * GW + GW / 2;
-        const int t = band * BH + BH / 2;
-        const int steps = right ? (GW - GW / 2 - 1) : (GW / 2);
-        int cu = s - xmin;
-        const int cv = t - ymin;
-        int p = med[t * TX + s];
-        constexpr int kRowsPerLane = (kMaxExtent + 31) / 32;
-        int eo[kRowsPerLane], lo[kRowsPerLane];  // this lane's rows: entering / leaving offsets
-#pragma unroll
-        for (int q = 0; q < kRowsPerLane; ++q) {
-            const int i = lane + 32 * q;
-            eo[q] = lo[q] = 0;  // rows beyond the kernel compare the centre with itself: no change
-            if (i < P.nrows) {
-                const int2 o = htab[i];
-                eo[q] = right ? o.y : o.x - 1;
-                lo[q] = right ? o.x : o.y - 1;
+            for (int k = 0; k < steps; ++k) {
+                const uint16_t* ctr = ord + cv * SP + cu;
+                int d = 0;
+    #pragma unroll
+                for (int q = 0; q < kRowsPerLane; ++q)
+                    if (32 * q < P.nrows) d += (int)(ctr[eo[q]] < p) - (int)(ctr[lo[q]] < p);
+                d = __reduce_add_sync(kFull, d);
+                // targets of the pivot's window and of the next one (re-read: no extra live state)
+                const int tp = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
+                cu += right ? 1 : -1;
+                s += right ? 1 : -1;
+                const int tn = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
+                const int m = ballot_select(om, N, p, tp + d, tn, cu - cx0, cv - cy0, member);
+                if (m < 0) set_status(FIM_ERR_INTERNAL);
+                p = max(m, 0);
+                if (lane == 0) med[t * TX + s] = (uint16_t)p;
             }
         }
-        for (int k = 0; k < steps; ++k) {
-            const uint16_t* ctr = ord + cv * SP + cu;
-            int d = 0;
-#pragma unroll
-            for (int q = 0; q < kRowsPerLane; ++q)
-                if (32 * q < P.nrows) d += (int)(ctr[eo[q]] < p) - (int)(ctr[lo[q]] < p);
-            d = __reduce_add_sync(kFull, d);
-            cu += right ? 1 : -1;
-            s += right ? 1 : -1;
-            const int m = ballot_select(om, N, p, target + d, target, cu - cx0, cv - cy0, member);
-            if (m < 0) set_status(FIM_ERR_INTERNAL);
-            p = max(m, 0);
-            if (lane == 0) med[t * TX + s] = (uint16_t)p;
-        }
-    }
-    G.sync();
+        G.sync();
 
-    // ---- 5. vertical sweeps: thread per window column, per-thread refinement ----------------
-    stamp(P, tile, 5, G);
-    if (warp < P.vthreads / 32) {
-        const int groups = TX / 32;
-        const int cg = warp % groups;
-        const int rest = warp / groups;
-        const int band = P.vmix ? (rest + lane) % P.RB : rest % P.RB;  // per lane with mixing
-        const int down = rest / P.RB;  // 0: up, 1: down
-        const int s = cg * 32 + lane;
-        int t = band * BH + BH / 2;
-        const int steps = down ? (BH - BH / 2 - 1) : (BH / 2);
-        const int cu = s - xmin;
-        int cv = t - ymin;
-        int p = med[t * TX + s];
-        const int ncols = P.ncols;
-        const int scan_groups = P.scan_groups;
-        const int eoff = down ? 0 : -SP;
-        for (int k = 0; k < steps; ++k) {
-            const uint16_t* ctr = ord + cv * SP + cu + eoff;
-            int d = 0;
-            if (down) {
-#pragma unroll 4
-                for (int j = 0; j < ncols; ++j) {
-                    const int2 o = vtab[j];
-                    d += (int)(ctr[o.y] < p) - (int)(ctr[o.x] < p);
+        // ---- 5. vertical sweeps: thread per window column, per-thread refinement ----------------
+        stamp(P, tile, 5, G);
+        if (warp < P.vthreads / 32) {
+            const int groups = TX / 32;
+            const int cg = warp % groups;
+            const int rest = warp / groups;
+            const int band = P.vmix ? (rest + lane) % P.RB : rest % P.RB;  // per lane with mixing
+            const int down = rest / P.RB;  // 0: up, 1: down
+            const int s = cg * 32 + lane;
+            int t = band * BH + BH / 2;
+            const int steps = down ? (BH - BH / 2 - 1) : (BH / 2);
+            const int cu = s - xmin;
+            int cv = t - ymin;
+            int p = med[t * TX + s];
+            const int ncols = P.ncols;
+            const int scan_groups = P.scan_groups;
+            const int eoff = down ? 0 : -SP;
+            for (int k = 0; k < steps; ++k) {
+                const uint16_t* ctr = ord + cv * SP + cu + eoff;
+                int d = 0;
+                if (down) {
+    #pragma unroll 4
+                    for (int j = 0; j < ncols; ++j) {
+                        const int2 o = vtab[j];
+                        d += (int)(ctr[o.y] < p) - (int)(ctr[o.x] < p);
+                    }
+                } else {
+    #pragma unroll 4
+                    for (int j = 0; j < ncols; ++j) {
+                        const int2 o = vtab[j];
+                        d += (int)(ctr[o.x] < p) - (int)(ctr[o.y] < p);
+                    }
                 }
-            } else {
-#pragma unroll 4
-                for (int j = 0; j < ncols; ++j) {
-                    const int2 o = vtab[j];
-                    d += (int)(ctr[o.x] < p) - (int)(ctr[o.y] < p);
-                }
+                const int tp = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
+                cv += down ? 1 : -1;
+                t += down ? 1 : -1;
+                const int tn = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
+                const int mine =
+                    thread_select<SHAPE, W, KS>(om, N, p, tp + d, tn, cu - cx0, cv - cy0, member, scan_groups);
+                if (mine < 0) set_status(FIM_ERR_INTERNAL);
+                p = max(mine, 0);
+                med[t * TX + s] = (uint16_t)p;
             }
-            cv += down ? 1 : -1;
-            t += down ? 1 : -1;
-            int mine;
-            mine = thread_select<SHAPE, W, KS>(om, N, p, target + d, target, cu - cx0, cv - cy0, member, scan_groups);
-            if (mine < 0) set_status(FIM_ERR_INTERNAL);
-            p = max(mine, 0);
-            med[t * TX + s] = (uint16_t)p;
         }
-    }
-    G.sync();
+        G.sync();
 
-    // ---- 6. output: the input value at Omega[m] ------------------------------------------------
-    stamp(P, tile, 6, G);
-    const Img im(P);
-    char* out = static_cast<char*>(P.out);
-    const int txshift = P.txshift;
-    for (int idx = tid; idx < TX * TY; idx += nthreads) {
-        const int t = idx >> txshift, s = idx & (TX - 1);
-        const int gx = tx0 + s, gy = ty0 + t;
-        if (gx >= im.w || gy >= im.h) continue;
-        const uint32_t e = om[med[idx]];
-        const V val = load_px<DT>(im, gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
-        reinterpret_cast<V*>(out + (long long)gy * im.pitch)[gx] = val;
+        // ---- 6. output: the input value at Omega[m] ------------------------------------------------
+        stamp(P, tile, 6, G);
+        const Img im(P);
+        char* out = static_cast<char*>(q == 0 ? P.out : P.outs[q]);
+        const int txshift = P.txshift;
+        for (int idx = tid; idx < TX * TY; idx += nthreads) {
+            const int t = idx >> txshift, s = idx & (TX - 1);
+            const int gx = tx0 + s, gy = ty0 + t;
+            if (gx >= im.w || gy >= im.h) continue;
+            const uint32_t e = om[med[idx]];
+            const V val = load_px<DT>(im, gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
+            reinterpret_cast<V*>(out + (long long)gy * im.pitch)[gx] = val;
+        }
+        G.sync();
+        stamp(P, tile, 7, G);
     }
-    G.sync();
-    stamp(P, tile, 7, G);
 }
 
 __device__ __forceinline__ void load_tables(const Plan& P) {

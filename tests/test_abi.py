@@ -104,3 +104,24 @@ def test_argument_checks_need_no_gpu():
     # percentile outside [0, 100]
     assert lib.fim_percentile(a, a + 2048, 4, 4, 8, fim.FIM_U16, k.handle, 101.0, 0, None) == INVALID
     assert lib.fim_percentile(a, a + 2048, 4, 4, 8, fim.FIM_U16, k.handle, float("nan"), 0, None) == INVALID
+    # several percentiles: count outside 1..8, a null output, an output overlapping the input,
+    # a percentile outside [0, 100]
+    outs = (ctypes.c_void_p * 9)(*([a + 2048] * 9))
+    pcts = (ctypes.c_double * 9)(*([50.0] * 9))
+    for count in (0, 9):
+        assert lib.fim_percentiles(a, outs, pcts, count, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    assert lib.fim_percentiles(a, None, pcts, 2, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    assert lib.fim_percentiles(a, outs, None, 2, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    bad = (ctypes.c_void_p * 2)(a + 2048, None)
+    assert lib.fim_percentiles(a, bad, pcts, 2, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    bad = (ctypes.c_void_p * 2)(a + 2048, a + 16)
+    assert lib.fim_percentiles(a, bad, pcts, 2, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    badp = (ctypes.c_double * 2)(50.0, -1.0)
+    assert lib.fim_percentiles(a, outs, badp, 2, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    # percentile map: null, pitch below 4 * w or not a multiple of 4, overlapping the output
+    m = a + 3072
+    assert lib.fim_percentile_map(a, a + 2048, None, 16, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    assert lib.fim_percentile_map(a, a + 2048, m, 12, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    assert lib.fim_percentile_map(a, a + 2048, m, 18, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    assert lib.fim_percentile_map(a, a + 2048, a + 2040, 16, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    assert lib.fim_percentile_map(a, a + 2048, a + 2060, 16, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
