@@ -189,6 +189,8 @@ fim_status read_and_clear_k4_status();
 // (fim_tile_extras.cu) the kernels with the learned bracket, training rows and seed statistics
 fim_status launch_tile_kernel_extras(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_extras_status();
+fim_status launch_tile_kernel_map(Plan& p, cudaStream_t stream);
+fim_status read_and_clear_map_status();
 // Per-pixel target ranks of a percentile map (w x h floats, pitch in bytes) into `ranks`
 // (w x h ints, dense rows), on `stream`.
 fim_status launch_percentile_ranks(const float* pct, long long pct_pitch, int w, int h, int n, int* ranks,

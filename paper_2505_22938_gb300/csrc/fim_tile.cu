@@ -5,7 +5,8 @@
 namespace fim {
 
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
-    if (p.model != nullptr || p.samples != nullptr || p.stats != nullptr || p.nranks > 1 || p.rank_map != nullptr)
+    if (p.rank_map != nullptr) return launch_tile_kernel_map(p, stream);
+    if (p.model != nullptr || p.samples != nullptr || p.stats != nullptr || p.nranks > 1)
         return launch_tile_kernel_extras(p, stream);
     return p.scan_groups == 4 ? launch_tile_kernel_k4(p, stream) : launch_tile_kernel_ks<8>(p, stream);
 }
@@ -22,7 +23,10 @@ fim_status read_and_clear_device_status(cudaStream_t stream) {
     const fim_status b = read_and_clear_k4_status();
     const fim_status c = read_and_clear_batch_status();
     const fim_status d = read_and_clear_extras_status();
-    return a != FIM_OK ? a : (b != FIM_OK ? b : (c != FIM_OK ? c : d));
+    const fim_status e = read_and_clear_map_status();
+    for (fim_status x : {a, b, c, d, e})
+        if (x != FIM_OK) return x;
+    return FIM_OK;
 }
 
 }  // namespace fim

@@ -732,8 +732,9 @@ __device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, 
 // KS: omnigram groups per scan step of the vertical sweep, fixed at compile time (4 or 8), or
 // 0 to follow the plan's scan_groups at run time (the batch kernel, which serves every plan:
 // one run-time loop keeps its 18 inlined pipelines small enough to compile quickly).
-// XT: 1 compiles the extras — the learned bracket, training-row output and seed statistics —
-// which live in kernels of their own: at the 64-register cap of 1024-thread CTAs their code
+// XT: 1 compiles the extras — the learned bracket, training-row output, seed statistics and
+// several target ranks per launch — and 2 a target rank per output pixel (a percentile map).
+// Each lives in kernels of its own: at the 64-register cap of 1024-thread CTAs their code
 // changes how the compiler allocates the plain pipeline's registers, and the reverse.
 template <int DT, int SHAPE, int W, int OG, int KS = 0, int XT = 0>
 __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G) {
@@ -801,11 +802,11 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     }
     // Extras kernels may take several target ranks (percentiles) of one window size: the
     // ordinal transform and the ordinal image above are built once and serve them all.
-    const int nr = XT ? P.nranks : 1;
+    const int nr = XT == 1 ? P.nranks : 1;
     // With a percentile map every output pixel has its own target rank. A slide's pivot is the
     // previous window's result, which has exactly that window's target below it, so the count
     // at the pivot after the slide is the previous target plus the change.
-    const bool mapped = XT && P.rank_map != nullptr;
+    const bool mapped = XT == 2 && P.rank_map != nullptr;
     for (int q = 0; q < nr; ++q) {
         const int target = q == 0 ? P.rank : P.ranks[q];
         const int BH = TY / P.RB;      // band height
@@ -816,9 +817,9 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
         // (or, with a learned bracket, two exact counts at predicted ranks, then ballot refine)
         stamp(P, tile, 3, G);
-        const bool learned = XT && P.model != nullptr;
-        const bool sampling = XT && P.samples != nullptr;
-        const bool counting = XT && P.stats != nullptr;
+        const bool learned = XT == 1 && P.model != nullptr;
+        const bool sampling = XT == 1 && P.samples != nullptr;
+        const bool counting = XT == 1 && P.stats != nullptr;
         float* quant = reinterpret_cast<float*>(misc);  // the sort's scan scratch is free from here on
         if (learned || sampling) {
             if (warp == 0) {  // normalised value quantiles of the footprint: C at N (j + 1/2) / 32
