@@ -133,10 +133,10 @@ fim_status fim_percentile(const void* in, void* out, int w, int h, size_t pitch_
  * (the seeds, slides and scans run once per rank). outs: `count` (1..8) device pointers, host
  * array, each an output image with the input's pitch; percentiles: `count` values in [0, 100],
  * rank = round(percentile / 100 * (n - 1)) as in fim_percentile. Same argument checks and
- * errors as fim_percentile (every output must not overlap the input), plus
- * FIM_ERR_INVALID_ARG for count outside 1..8. Asynchronous on `stream`. Sec. 6.2 proposes
- * this extension (several percentiles, e.g. quartiles, from one ordinal transform); the
- * paper's own implementation filters one percentile at a time.
+ * errors as fim_percentile (no output may overlap the input; outputs that overlap one
+ * another race), plus FIM_ERR_INVALID_ARG for count outside 1..8. Asynchronous on `stream`.
+ * Sec. 6.2 proposes this extension (several percentiles, e.g. quartiles, from one ordinal
+ * transform); the paper's own implementation filters one percentile at a time.
  */
 fim_status fim_percentiles(const void* in, void* const* outs, const double* percentiles, int count, int w, int h,
                            size_t pitch_bytes, fim_dtype dtype, const fim_kernel* k, fim_border border, void* stream);
@@ -144,12 +144,15 @@ fim_status fim_percentiles(const void* in, void* const* outs, const double* perc
 /*
  * Spatially varying percentile (Fig. 14): every output pixel takes its own percentile from a
  * device float32 map. percentiles: w x h values, rows pct_pitch_bytes apart (>= 4 * w, a
- * multiple of 4); read only, owned by the caller, must not overlap the output. Each value is
+ * multiple of 4); read only, owned by the caller, must not overlap the output and must stay
+ * valid until the stream has run the call's work. Each value is
  * clamped to [0, 100] (NaN counts as 0) and rounded to a rank as in fim_percentile, in fp64:
  * floor(p / 100 * (n - 1) + 1/2). Slides carry the count at their pivot from one window's
  * rank to the next, so neighbouring pixels may differ by any amount. Same checks and errors
  * as fim_percentile, plus FIM_ERR_INVALID_ARG for a null map, a bad map pitch, or a map that
- * overlaps the output. Asynchronous on `stream`.
+ * overlaps the output, and FIM_ERR_OOM when the w x h int32 rank image (stream-ordered
+ * device memory, released on the stream after the filter) cannot be allocated. Asynchronous
+ * on `stream`.
  */
 fim_status fim_percentile_map(const void* in, void* out, const float* percentiles, size_t pct_pitch_bytes, int w,
                               int h, size_t pitch_bytes, fim_dtype dtype, const fim_kernel* k, fim_border border,
