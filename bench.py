@@ -226,10 +226,10 @@ def cpu_oracle_sample(img, rows: int):
 # ---------------------------------------------------------------------------------------------
 
 def batched_section(fim, torch, reps: int = 3):
-    """64 images (sides 512-4096, u8/u16/f32, disk r log-uniform in [2, 128]); tile shapes
-    autotuned per (dtype, radius) on a 512x512 crop (both forms use them); one CUDA-graph-
-    captured persistent launch against the same filters issued as one launch per image.
-    Outputs are compared bytewise."""
+    """64 images (sides 512-4096, u8/u16/f32, disk r log-uniform in [2, 128]) with the
+    library's tile shapes per (dtype, kernel extent) in both forms; one CUDA-graph-captured
+    persistent launch against the same filters issued as one launch per image. Outputs are
+    compared bytewise."""
     import datagen
     codes = {"u8": fim.FIM_U8, "u16": fim.FIM_U16, "f32": fim.FIM_F32}
     esz = {"u8": 1, "u16": 2, "f32": 4}
@@ -245,19 +245,6 @@ def batched_section(fim, torch, reps: int = 3):
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     sh = int(stream.cuda_stream)
-    # autotune every (dtype, radius) pair on a 512x512 crop of its first image
-    t0 = time.perf_counter()
-    tuned = {}
-    for j, x in zip(jobs, imgs):
-        key = (j["dtype"], j["r"])
-        if key in tuned:
-            continue
-        crop = x[:512, :512].contiguous()
-        tmp = torch.empty_like(crop)
-        args = (crop.data_ptr(), tmp.data_ptr(), crop.shape[1], crop.shape[0], crop.stride(0) * esz[j["dtype"]],
-                codes[j["dtype"]], kern[j["r"]], sh)
-        tuned[key] = fim.fim_autotune(*args)  # used by the single-image launches and the batch
-    tune_s = time.perf_counter() - t0
     cjobs = [fim.make_job(x.data_ptr(), o.data_ptr(), j["w"], j["h"], x.stride(0) * esz[j["dtype"]],
                           codes[j["dtype"]], kern[j["r"]]) for j, x, o in zip(jobs, imgs, outs_b)]
     batch = fim.fim_batch_create(cjobs, list(kern.values()))
@@ -291,9 +278,6 @@ def batched_section(fim, torch, reps: int = 3):
     ms_seq = timed(sequential)
     ms_bat = timed(g.replay)
     status = fim.fim_sync_status(sh)
-    # the shapes tuned on 512x512 crops belong to this section: later sections filter large
-    # images with the default plans
-    fim.fim_autotune_clear()
     same = all(torch.equal(a.view(torch.uint8), b.view(torch.uint8)) for a, b in zip(outs_b, outs_s))
     mpix = sum(j["w"] * j["h"] for j in jobs) / 1e6
     return {"workload": "64 images, sides U{512..4096}, dtypes u8/u16/f32, disk r log-uniform [2,128]",
@@ -301,7 +285,7 @@ def batched_section(fim, torch, reps: int = 3):
             "sequential_Mpix_s": mpix / (ms_seq * 1e-3), "speedup": ms_seq / ms_bat,
             "ms_batched_graph": ms_bat, "ms_sequential": ms_seq, "launches_batched": 1,
             "launches_sequential": len(jobs), "bit_exact_vs_sequential": bool(same), "status": status,
-            "tiles": batch.info["total_tiles"], "autotune_s": round(tune_s, 2), "generate_s": round(gen_s, 2)}
+            "tiles": batch.info["total_tiles"], "generate_s": round(gen_s, 2)}
 
 
 # ---------------------------------------------------------------------------------------------
