@@ -3,7 +3,13 @@
 
 Workload (one "step"): the 4096x4096 uint16 photo-like image, median-filtered with disk
 kernels of radius 8, 32 and 48 (clamp borders); 3 x 16.78 Mpix of output per step.
-Metric: output Mpix/s, bit-exact (every output is a selected input value).
+Metric: output Mpix/s, bit-exact (every output is a selected input value). A band of 1024
+full rows of the timed outputs is compared with the CPU oracle (the same band it is timed on).
+
+Sections after the headline (one GPU): the 8-bit 256x256 workload, a u16 radius sweep
+(r = 2..128) and the 8192x8192 float workload (disk r = 64/100, hexagon, ellipse), each with
+Mpix/s, a roofline fraction and whole rows checked against the oracle; then the batched,
+several-percentile and learned-bracket comparisons. Any parity mismatch fails the run.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -47,6 +53,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-image batched comparison")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bracket comparison")
     ap.add_argument("--no-multi", action="store_true", help="skip the several-percentiles comparison")
+    ap.add_argument("--no-sections", action="store_true",
+                    help="skip the radius sweep and the 8-bit and float workloads")
     ap.add_argument("--train-images", type=int, default=200)
     ap.add_argument("--profile-case", default=None, metavar="SIDE:R",
                     help="only run two launches on a SIDE x SIDE crop of the image at radius R (for ncu)")
@@ -161,14 +169,26 @@ class ClockSampler:
 # algorithmic work (element operations per output pixel) for the roofline
 # ---------------------------------------------------------------------------------------------
 
-def algorithmic_ops_per_pixel(r: int, footprint: int, tile_w: int, tile_h: int, passes: int = 1) -> float:
-    """Element operations per output pixel of the disk filter: the ordinal transform touches
-    every footprint pixel once per sort pass (16-bit data: one counting-sort pass in 1024-thread
-    CTAs, two radix passes in smaller ones), a
-    vertical slide compares the 2*(2r+1) entering and leaving pixels, and the omnigram
-    refinement tests at least one 64-entry block (the minimum when the median stays within its
-    pivot quantum). Each element operation needs at least one integer instruction."""
-    return footprint / (tile_w * tile_h) * passes + 2 * (2 * r + 1) + 64
+def algorithmic_ops_per_pixel(r: int, footprint: int, tile_w: int, tile_h: int, passes: int = 1,
+                              width: int | None = None) -> float:
+    """Element operations per output pixel: the ordinal transform touches every footprint
+    pixel once per sort pass (8-bit data and 16-bit data in 1024-thread CTAs: one counting-sort
+    pass; 16-bit data in smaller CTAs: two radix passes; float: three in 1024-thread CTAs, a 16-bit
+    counting pass and two 8-bit passes, else four), a vertical slide
+    compares the 2 * width entering and leaving pixels (width = 2r + 1 for a disk), and the
+    omnigram refinement tests at least one 64-entry block (the minimum when the median stays
+    within its pivot quantum). Each element operation needs at least one integer instruction."""
+    w = 2 * r + 1 if width is None else width
+    return footprint / (tile_w * tile_h) * passes + 2 * w + 64
+
+
+def sort_passes(dtype: str, threads: int) -> int:
+    """Key passes of the ordinal transform the library runs for a plan (see the docstring above)."""
+    if dtype == "f32":  # full CTAs: one 16-bit counting pass + two 8-bit passes
+        return 3 if threads >= 1024 else 4
+    if dtype == "u16" and threads < 1024:
+        return 2
+    return 1
 
 
 def peak_alu_ops(clock_mhz: float) -> float:
@@ -202,7 +222,9 @@ def profiled_traffic():
 # CPU oracle baseline (bounded sample of the same workload)
 # ---------------------------------------------------------------------------------------------
 
-def cpu_oracle_sample(img, rows: int):
+def cpu_oracle_sample(img, rows: int, gpu_outs=None):
+    """Times the oracle on a band of full rows of the bench image at every radius; with the
+    GPU outputs of the same launches, also compares every pixel of the band with them."""
     import numpy as np
 
     import oracle
@@ -212,13 +234,178 @@ def cpu_oracle_sample(img, rows: int):
     ys = ys.ravel().astype(np.int32)
     cores = oracle.max_threads()
     t0 = time.perf_counter()
-    for r in RADII:
-        oracle.median_points(img, oracle.disk_offsets(r), xs, ys)
+    res = [oracle.median_points(img, oracle.disk_offsets(r), xs, ys) for r in RADII]
     dt = time.perf_counter() - t0
     px = len(xs) * len(RADII)
-    return {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+    base = {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
             "sample": f"rows {y0}..{y0 + rows - 1} x all 4096 columns of the same image at r=8,32,48 "
                       f"({px} output pixels, {dt:.1f} s)"}
+    parity = None
+    if gpu_outs is not None:
+        bad = 0
+        for exp, got in zip(res, gpu_outs):
+            band = got[y0:y0 + rows].view(torch_int16()).cpu().numpy().view(np.uint16).ravel()
+            bad += int(np.count_nonzero(band != exp))
+        parity = {"pixels": px, "mismatches": bad, "tolerance": "0 (bit-exact)",
+                  "what": f"GPU outputs of the last timed step, rows {y0}..{y0 + rows - 1} x 4096 columns, "
+                          f"r=8,32,48, against the CPU oracle"}
+    return base, parity
+
+
+def torch_int16():
+    import torch
+    return torch.int16
+
+
+def timed_launch_ms(torch, fn, reps: int, flush) -> float:
+    """Median CUDA-event time of fn() on the current stream, L2 flushed before each call."""
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def band_parity(img_host, out_dev, offsets, rows, rank=None):
+    """Compares whole rows of a GPU output with the oracle; returns (pixels, mismatches)."""
+    import numpy as np
+
+    import oracle
+    h, w = img_host.shape
+    ys = np.repeat(np.asarray(rows, dtype=np.int32), w)
+    xs = np.tile(np.arange(w, dtype=np.int32), len(rows))
+    exp = oracle.median_points(img_host, offsets, xs, ys, rank=rank)
+    if out_dev.dtype == torch_uint16():  # index an int16 view: few ops support uint16 tensors
+        got = out_dev.view(torch_int16())[list(rows)].cpu().numpy().view(np.uint16)
+    else:
+        got = out_dev[list(rows)].cpu().numpy()
+    ui = {1: np.uint8, 2: np.uint16, 4: np.uint32}[got.dtype.itemsize]
+    return int(len(xs)), int(np.count_nonzero(got.ravel().view(ui) != exp.view(ui)))
+
+
+def torch_uint16():
+    import torch
+    return torch.uint16
+
+
+# ---------------------------------------------------------------------------------------------
+# radius sweep (u16), the float / non-circular workload, the tiny 8-bit workload
+# ---------------------------------------------------------------------------------------------
+
+SWEEP_RADII = (2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128)
+
+
+def roofline_entry(fim, kernel, code, dtype, w, h, ms, r, width, clock_mhz):
+    plan = fim.fim_plan_info(kernel, code, w, h)
+    ops = algorithmic_ops_per_pixel(r, plan["footprint"], plan["tile_w"], plan["tile_h"],
+                                    sort_passes(dtype, plan["threads"]), width)
+    frac = ops * w * h / (ms * 1e-3) / peak_alu_ops(clock_mhz)
+    return {"ms": round(ms, 4), "Mpix_s": round(w * h / ms / 1e3, 1), "tile": f'{plan["tile_w"]}x{plan["tile_h"]}',
+            "threads": plan["threads"], "footprint": plan["footprint"], "ops_per_px": round(ops, 1),
+            "roofline_frac": round(frac, 4)}
+
+
+def sweep_section(fim, torch, src, img_host, flush, clock_mhz, reps: int = 5):
+    """u16 4096x4096 photo-like, disk r in SWEEP_RADII: Mpix/s and roofline fraction per radius,
+    with two whole rows per radius (the first row and the middle one) checked against the oracle."""
+    import oracle
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    out = torch.empty_like(src)
+    res, px_all, bad_all = {}, 0, 0
+    for r in SWEEP_RADII:
+        k = fim.fim_create_kernel_circle(r)
+
+        def run():
+            fim.fim_median(src.data_ptr(), out.data_ptr(), W, H, W * 2, fim.FIM_U16, k, sh)
+
+        run()
+        ms = timed_launch_ms(torch, run, reps, flush)
+        e = roofline_entry(fim, k, fim.FIM_U16, "u16", W, H, ms, r, None, clock_mhz)
+        px, bad = band_parity(img_host, out, oracle.disk_offsets(r), (0, H // 2 + 17))
+        e["parity_pixels"], e["parity_mismatches"] = px, bad
+        px_all += px
+        bad_all += bad
+        res[f"r{r}"] = e
+    return {"workload": "u16 4096x4096 photo-like, disk r = " + ",".join(map(str, SWEEP_RADII)),
+            "per_radius": res, "parity": {"pixels": px_all, "mismatches": bad_all},
+            "status": fim.fim_sync_status(sh)}
+
+
+def config3_section(fim, torch, flush, clock_mhz, reps: int = 3):
+    """f32 8192x8192 (smoothed Gaussian fields + 1 % Cauchy outliers): disk r = 64 and 100, a
+    hexagon of circumradius 64 and an 80x40 ellipse; four whole rows each (two at the top border)
+    checked against the oracle."""
+    import numpy as np
+
+    import datagen
+    import oracle
+    n = 8192
+    img = datagen.torch_field_f32(datagen.seed_for(3, 0), n, n)
+    host = img.cpu().numpy()
+    out = torch.empty_like(img)
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    hexv = oracle.regular_polygon_vertices(6, 64.0)
+    cases = [("disk_r64", fim.fim_create_kernel_circle(64), oracle.disk_offsets(64), 64, None),
+             ("disk_r100", fim.fim_create_kernel_circle(100), oracle.disk_offsets(100), 100, None),
+             ("hexagon_R64", fim.fim_create_kernel_polygon(hexv.tolist()), oracle.polygon_offsets(hexv), 64, 129),
+             ("ellipse_80x40", fim.fim_create_kernel_ellipse(80, 40), oracle.ellipse_offsets(80, 40), 80, 161)]
+    res, px_all, bad_all = {}, 0, 0
+    for name, k, off, r, width in cases:
+        def run():
+            fim.fim_median(img.data_ptr(), out.data_ptr(), n, n, n * 4, fim.FIM_F32, k, sh)
+
+        run()
+        ms = timed_launch_ms(torch, run, reps, flush)
+        e = roofline_entry(fim, k, fim.FIM_F32, "f32", n, n, ms, r, width, clock_mhz)
+        px, bad = band_parity(host, out, off, (0, 1, n // 2, n - 1))
+        e["parity_pixels"], e["parity_mismatches"] = px, bad
+        px_all += px
+        bad_all += bad
+        res[name] = e
+    del img, out
+    return {"workload": "f32 8192x8192 Gaussian fields + 1% Cauchy(0,10) outliers; disk r64/r100, hexagon R64, "
+                        "ellipse 80x40", "per_kernel": res, "parity": {"pixels": px_all, "mismatches": bad_all},
+            "status": fim.fim_sync_status(sh)}
+
+
+def config1_section(fim, torch, reps: int = 20):
+    """u8 256x256 uniform noise, disk r = 4: the whole output against the oracle; the time is
+    the mean of back-to-back calls (a launch-bound size)."""
+    import numpy as np
+
+    import datagen
+    import oracle
+    host = datagen.config1_image()
+    img = torch.from_numpy(host).cuda()
+    out = torch.empty_like(img)
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    k = fim.fim_create_kernel_circle(4)
+
+    def run():
+        fim.fim_median(img.data_ptr(), out.data_ptr(), 256, 256, 256, fim.FIM_U8, k, sh)
+
+    run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        run()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    exp = oracle.median_filter(host, oracle.disk_offsets(4))
+    bad = int(np.count_nonzero(out.cpu().numpy() != exp))
+    return {"workload": "u8 256x256 uniform, disk r=4 (49 taps)", "ms": round(ms, 4),
+            "Mpix_s": round(256 * 256 / ms / 1e3, 1),
+            "parity": {"pixels": 256 * 256, "mismatches": bad, "what": "whole image"},
+            "status": fim.fim_sync_status(sh)}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -586,7 +773,7 @@ def run_native(args):
         lm = [l[i] for l in launch_ms]
         avg = sum(lm) / len(lm)
         plan = fim.fim_plan_info(kernels[i], fim.FIM_U16, W, H)
-        passes = 1 if plan["threads"] >= 1024 else 2  # 16-bit counting sort, or two radix passes
+        passes = sort_passes("u16", plan["threads"])
         ops = algorithmic_ops_per_pixel(r, plan["footprint"], plan["tile_w"], plan["tile_h"], passes) * H * W
         tot_ops += ops
         tot_ms += avg
@@ -614,20 +801,37 @@ def run_native(args):
         "roofline": roofline,
         "clocks": clk,
     }
+    failed = []
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's band is also a full-size parity check of the timed launches' outputs
+        line["cpu_baseline"], line["parity"] = cpu_oracle_sample(img, args.cpu_rows, outs)
+        if line["parity"]["mismatches"]:
+            failed.append("parity")
+    if world == 1 and not args.no_sections:
+        sec_clocks = ClockSampler(torch.cuda.current_device())
+        sec_clocks.start()
+        time.sleep(0.2)
+        line["config1"] = config1_section(fim, torch)
+        line["sweep_u16"] = sweep_section(fim, torch, src, img, flush, clock_for_peak)
+        line["config3"] = config3_section(fim, torch, flush, clock_for_peak)
+        line["sections_clocks"] = sec_clocks.stop()
+        for name in ("config1", "sweep_u16", "config3"):
+            if line[name]["parity"]["mismatches"] or line[name]["status"]:
+                failed.append(name)
     if world == 1 and not args.no_batched:
         line["batched"] = batched_section(fim, torch)
     if world == 1 and not args.no_multi:
         line["percentiles"] = multi_percentile_section(fim, torch, src)
     if world == 1 and not args.no_learned:
         line["learned"] = learned_section(fim, torch, args.train_images)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(img, args.cpu_rows)
+    if failed:
+        line["failed"] = failed
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
-    return 0
+    return 1 if failed else 0
 
 
 def main():

@@ -109,7 +109,9 @@ fim_status fim_median(const void* in, void* out, int w, int h, size_t pitch_byte
  * Same arguments and result as fim_median. Its workspace is one fixed array of
  * FIM_NOALLOC_WORKSPACE_BYTES of device memory inside the library, held by every GPU that loads
  * the library until the process exits. The first call on each device looks up the array's
- * address (cudaGetSymbolAddress); make that first call before any stream capture. Calls needing
+ * address (cudaGetSymbolAddress) and keeps it for the life of the process; make that first call
+ * before any stream capture. A cudaDeviceReset of that device invalidates the kept address: do
+ * not call this entry point on the device again in the same process after one. Calls needing
  * more workspace than the array holds (large kernels on large images: the per-CTA buffers of
  * kernels whose footprint does not fit in shared memory) return FIM_ERR_UNSUPPORTED and launch
  * nothing. All calls share the array, so calls whose work overlaps on the GPU (different streams
@@ -213,7 +215,9 @@ typedef struct fim_batch fim_batch;
 /*
  * Plans a batch: validates every job, picks tile configurations (tuned ones when available),
  * uploads the per-job plans and allocates the batch's workspace. Synchronous. The images are
- * only referenced: they must stay valid while the batch runs.
+ * only referenced: they must stay valid while the batch runs. Every job runs in the same launch,
+ * so an output may overlap neither another output nor any job's input (its own included):
+ * FIM_ERR_INVALID_ARG. Several jobs may share one input.
  */
 fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out);
 
@@ -340,7 +344,8 @@ const char* fim_version(void);
 /*
  * Diagnostics. Attaches a device buffer of tiles * 8 uint64 that every following filter
  * launch (from any thread) fills with clock64() stamps at its phase boundaries: load, sort,
- * structure build, seeds, seed rows, vertical sweeps, output, end; one row of 8 per tile
+ * structure build, seeds, seed rows, vertical sweeps (which also write the output), the end of
+ * the first thread's own sweep, end of the tile; one row of 8 per tile
  * index below `tiles`. fim_debug_phase_clocks(NULL, 0) detaches it. The buffer stays owned
  * by the caller and must outlive the launches that use it.
  */

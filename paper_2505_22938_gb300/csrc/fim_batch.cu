@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <iterator>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -31,8 +32,38 @@ int esize(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); 
 // Relative cost of one tile, used only to start the expensive tiles first.
 double tile_cost(const Plan& p) {
     const double px = (double)p.Tx * p.Ty;
-    const double sort = p.sort == kSortRadix ? 12.0 : 3.0;
+    const double sort = p.sort == kSortRadix ? 12.0 : (p.sort == kSortRadix16 ? 8.0 : 3.0);
     return p.N * sort + px * (2.0 * p.ncols + 80.0) + (double)p.RB * p.G * p.n * 2.0;
+}
+
+// Byte range [lo, hi) an image of one job occupies.
+struct Span {
+    uintptr_t lo, hi;
+};
+
+Span image_span(const void* base, const fim_job& j) {
+    const uintptr_t lo = (uintptr_t)base;
+    return Span{lo, lo + j.pitch_bytes * (size_t)(j.h - 1) + (size_t)j.w * (size_t)esize(j.dtype)};
+}
+
+// All jobs of a batch run in one launch, so no output may overlap another output or any input
+// (its own job's included): a tile would read pixels another tile has already overwritten.
+// Several jobs may read one input. O(n log n): sort the outputs, check neighbours, then look up
+// each input among them.
+bool batch_aliases(const fim_job* jobs, int count) {
+    std::vector<Span> outs((size_t)count);
+    for (int i = 0; i < count; ++i) outs[i] = image_span(jobs[i].out, jobs[i]);
+    std::sort(outs.begin(), outs.end(), [](const Span& a, const Span& b) { return a.lo < b.lo; });
+    for (int i = 1; i < count; ++i)
+        if (outs[i].lo < outs[i - 1].hi) return true;
+    for (int i = 0; i < count; ++i) {
+        const Span in = image_span(jobs[i].in, jobs[i]);
+        // the last output starting below the input's end is the only one that can reach into it
+        auto it = std::lower_bound(outs.begin(), outs.end(), in.hi,
+                                   [](const Span& s, uintptr_t v) { return s.lo < v; });
+        if (it != outs.begin() && std::prev(it)->hi > in.lo) return true;
+    }
+    return false;
 }
 
 void free_batch(fim_batch* b) {
@@ -50,8 +81,6 @@ extern "C" {
 fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
     if (!out || !jobs || count <= 0) return FIM_ERR_INVALID_ARG;
     *out = nullptr;
-    const int limit = device_smem_limit();
-    if (limit <= 0) return FIM_ERR_CUDA;
     constexpr int kCta = 1024;  // every batch CTA; jobs with smaller configurations run several groups
     std::vector<Plan> plans((size_t)count);
     for (int i = 0; i < count; ++i) {
@@ -61,6 +90,12 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
         const size_t es = (size_t)esize(j.dtype);
         if (j.pitch_bytes < (size_t)j.w * es || j.pitch_bytes % es != 0) return FIM_ERR_INVALID_ARG;
         if (!(j.percentile < 0.0 || j.percentile <= 100.0)) return FIM_ERR_INVALID_ARG;
+    }
+    if (batch_aliases(jobs, count)) return FIM_ERR_INVALID_ARG;
+    const int limit = device_smem_limit();
+    if (limit <= 0) return FIM_ERR_CUDA;
+    for (int i = 0; i < count; ++i) {
+        const fim_job& j = jobs[i];
         TileShape ts;
         fim_status s = choose_tile(j.kernel, j.dtype, limit, &ts);
         if (s != FIM_OK) return s;

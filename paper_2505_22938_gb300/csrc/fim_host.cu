@@ -256,6 +256,9 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     // The 65536 bins of the 16-bit counting sort (128 KiB) leave room for one CTA per SM, which
     // only a full 1024-thread CTA uses well; smaller CTAs sort 16-bit data by two radix passes.
     if (dtype == FIM_U16 && p->threads < 1024) p->sort = kSortRadix;
+    // Float keys in full CTAs: the 65536 bins sort the low half of the key in one pass, which
+    // replaces two of the four 8-bit passes (the layout falls back to four when they do not fit).
+    if (dtype == FIM_F32 && p->threads >= 1024) p->sort = kSortRadix16;
     // Placement. Tables, the ordinal image, medians and histograms always live in shared memory;
     // the omnigram, the radix keys and the radix position lists go to the CTA's global scratch
     // slice when shared memory cannot hold them (large kernels).
@@ -299,7 +302,7 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
         return gloc(o);
     };
     size_t smem = 0;
-    if (p->sort != kSortRadix) {
+    if (p->sort == kSortCount8 || p->sort == kSortCount16) {
         const size_t bins = p->sort == kSortCount8 ? 256 * 4 : 32768 * 4;
         const size_t uni = std::max(bins, solve_bytes);
         const bool om_smem = !p->wide && tab + om_bytes + uni <= (size_t)smem_limit;
@@ -318,15 +321,22 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
     } else {
         const size_t keys_bytes = align16((size_t)p->S * p->SH * 4);
         const size_t hist_bytes = align16((size_t)p->nwarps * (kSortBins + 1) * 4);
-        // try: everything in shared memory; keys in global; keys and lists in global
+        // try: everything in shared memory; keys in global; keys and lists in global. The 16-bit
+        // first pass's bins alias list A and the histograms, which are only used after it.
         int mode = 0;
-        for (mode = 0; mode < 3; ++mode) {
-            if (mode < 2 && p->wide) continue;  // 32-bit lists of a wide box never fit
-            size_t need = tab;
-            if (mode < 2) need += om_bytes;       // B / omnigram
-            const size_t sort_part = (mode == 0 ? keys_bytes : 0) + (mode < 2 ? om_bytes : 0) + hist_bytes;
-            need += std::max(sort_part, solve_bytes);
-            if (need <= (size_t)smem_limit) break;
+        for (;;) {
+            const size_t bins_bytes = p->sort == kSortRadix16 ? 32768 * 4 : 0;
+            for (mode = 0; mode < 3; ++mode) {
+                if (mode < 2 && p->wide) continue;  // 32-bit lists of a wide box never fit
+                size_t need = tab;
+                if (mode < 2) need += om_bytes;       // B / omnigram
+                const size_t sort_part =
+                    (mode == 0 ? keys_bytes : 0) + std::max((mode < 2 ? om_bytes : 0) + hist_bytes, bins_bytes);
+                need += std::max(sort_part, solve_bytes);
+                if (need <= (size_t)smem_limit) break;
+            }
+            if (mode < 3 || p->sort != kSortRadix16) break;
+            p->sort = kSortRadix;  // no room for the 65536 bins: four 8-bit passes
         }
         if (mode == 3) return FIM_ERR_UNSUPPORTED;
         size_t off = tab;
@@ -350,8 +360,10 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
         } else {
             p->loc_a = take_glob(om_bytes);
         }
+        p->loc_bins = p->loc_a >= 0 ? p->loc_a : (int)off;  // start of list A's and the histograms' region
         p->loc_hist = (int)off;
         off += hist_bytes;
+        if (p->sort == kSortRadix16) off = std::max(off, (size_t)p->loc_bins + 32768 * 4);
         p->loc_ord = (int)uni;
         p->loc_med = (int)(uni + ord_bytes);
         p->loc_shist = (int)(uni + ord_bytes + med_bytes);

@@ -51,7 +51,9 @@ struct TileShape {
 enum SortKind : int {
     kSortCount8 = 0,   // 256-bin counting sort (8-bit data)
     kSortCount16 = 1,  // 65536-bin counting sort with packed 16-bit bins (16-bit data, Eq. 5)
-    kSortRadix = 2     // stable LSD radix sort, 8-bit passes (four for float keys, two for 16-bit data)
+    kSortRadix = 2,    // stable LSD radix sort, 8-bit passes (four for float keys, two for 16-bit data)
+    kSortRadix16 = 3   // float keys in 1024-thread CTAs: 65536-bin counting pass on the low 16 bits,
+                       // then two stable 8-bit passes
 };
 
 // Everything a tile kernel launch needs, passed by value as a __grid_constant__ parameter.
@@ -184,7 +186,8 @@ fim_status read_and_clear_device_status(cudaStream_t stream);
 fim_status read_and_clear_batch_status();  // (fim_batch_kernel.cu) called by the above after its sync
 // (fim_tile_k4.cu) the kernels with 4 omnigram groups per scan step, and their status word
 fim_status launch_tile_kernel_k4(Plan& p, cudaStream_t stream);
-fim_status launch_tile_kernel_fixed_k4(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
+fim_status launch_tile_kernel_fixed_k4(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream,
+                                       bool launch);
 fim_status read_and_clear_k4_status();
 // (fim_tile_extras.cu) the kernels with the learned bracket, training rows and seed statistics
 fim_status launch_tile_kernel_extras(Plan& p, cudaStream_t stream);
@@ -195,7 +198,10 @@ fim_status read_and_clear_map_status();
 // (w x h ints, dense rows), on `stream`.
 fim_status launch_percentile_ranks(const float* pct, long long pct_pitch, int w, int h, int n, int* ranks,
                                    cudaStream_t stream);
-fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream);
+// Launch on a fixed workspace; FIM_ERR_UNSUPPORTED when it needs more than `capacity` bytes. With
+// `launch` false, only that check (FIM_OK: it fits).
+fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream,
+                                    bool launch = true);
 fim_status batch_prepare(int smem);
 fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);
 fim_status batch_launch(const BatchArgs& a, int grid, int threads, int smem, cudaStream_t stream);

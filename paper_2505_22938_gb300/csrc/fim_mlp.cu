@@ -8,7 +8,7 @@
 // Training minimises the Gaussian negative log-likelihood 0.5 (y - mu)^2 / sigma^2 + log sigma
 // with Adam on fp32 master weights; every forward and backward pass uses the bf16-rounded
 // weights (straight-through for the rounding). The filter uses mu +- z sigma as a bracket that
-// the exact selection verifies by counting (see the seed phase in fim_tile.cu): the network can
+// the exact selection verifies by counting (the seed phase of fim_tile_pipeline.cuh): the network can
 // only change how far the omnigram scan walks, never the output.
 #include <math.h>
 #include <stdio.h>

@@ -44,17 +44,21 @@ fim_status workspace_address(unsigned char** out) {
     return FIM_OK;
 }
 
-// Default tile choice of the library (without the autotuner's cache, whose lookup allocates),
-// probing each candidate into the caller's plan storage.
-fim_status pick_tile(const fim_kernel* k, int dtype, int limit, fim::Plan* probe, fim::TileShape* ts) {
-    static const fim::TileShape cands[] = {{64, 128, 8, 2}, {64, 64, 8, 2}, {32, 64, 8, 2}, {32, 32, 8, 2},
-                                           {32, 16, 8, 2}};
+// The library's default tile shapes, in its order of preference by kernel extent (small kernels:
+// 32x32 tiles in small CTAs first), without the autotuner's cache, whose lookup allocates. A
+// candidate is taken when it fits shared memory and its launch fits the fixed array (per-CTA
+// buffers of large kernels times the resident CTAs); the plan is built in the caller's storage.
+fim_status pick_plan(const fim_kernel* k, int dtype, int w, int h, int limit, fim::Plan* plan) {
+    static const fim::TileShape cands[] = {{32, 32, 2, 1}, {32, 32, 4, 1}, {64, 128, 8, 2}, {64, 64, 8, 2},
+                                           {32, 64, 8, 2}, {32, 32, 8, 2}, {32, 16, 8, 2}};
     const int extent = (k->xmax - k->xmin > k->ymax - k->ymin ? k->xmax - k->xmin : k->ymax - k->ymin) + 1;
-    for (int i = extent >= 81 ? 0 : 1; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
-        if (fim::make_plan(k, dtype, 0, 1, 1, cands[i], limit, probe) == FIM_OK && probe->smem_bytes <= limit) {
-            *ts = cands[i];
+    const int first = extent <= 33 ? 0 : (extent <= 45 ? 1 : (extent >= 65 ? 2 : 3));
+    for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
+        if (fim::make_plan(k, dtype, (k->n - 1) / 2, w, h, cands[i], limit, plan) != FIM_OK ||
+            plan->smem_bytes > limit)
+            continue;
+        if (fim::launch_tile_kernel_fixed(*plan, nullptr, FIM_NOALLOC_WORKSPACE_BYTES, nullptr, false) == FIM_OK)
             return FIM_OK;
-        }
     }
     return FIM_ERR_UNSUPPORTED;
 }
@@ -81,11 +85,8 @@ extern "C" fim_status fim_median_noalloc(const void* in, void* out, int w, int h
     if (s != FIM_OK) return s;
     // the plan lives in this thread's storage: no heap allocation on the call path
     static thread_local fim::Plan plan;
-    fim::TileShape ts;
-    s = pick_tile(k, dtype, limit, &plan, &ts);
-    if (s != FIM_OK) return s;
-    s = fim::make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, limit, &plan);
-    if (s != FIM_OK) return s;
+    s = pick_plan(k, dtype, w, h, limit, &plan);
+    if (s != FIM_OK) return s;  // no tile shape fits the fixed array: FIM_ERR_UNSUPPORTED
     plan.in = in;
     plan.out = out;
     plan.pitch = (long long)pitch_bytes;

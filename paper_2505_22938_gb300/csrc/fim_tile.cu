@@ -11,9 +11,10 @@ fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
     return p.scan_groups == 4 ? launch_tile_kernel_k4(p, stream) : launch_tile_kernel_ks<8>(p, stream);
 }
 
-fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
-    return p.scan_groups == 4 ? launch_tile_kernel_fixed_k4(p, scratch, capacity, stream)
-                              : launch_tile_kernel_fixed_ks<8>(p, scratch, capacity, stream);
+fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream,
+                                    bool launch) {
+    return p.scan_groups == 4 ? launch_tile_kernel_fixed_k4(p, scratch, capacity, stream, launch)
+                              : launch_tile_kernel_fixed_ks<8>(p, scratch, capacity, stream, launch);
 }
 
 fim_status read_and_clear_device_status(cudaStream_t stream) {

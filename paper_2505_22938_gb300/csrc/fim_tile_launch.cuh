@@ -55,9 +55,10 @@ fim_status launch_typed(Plan& p, cudaStream_t stream) {
 }
 
 // Same launch, but on a caller-provided workspace of fixed capacity (no allocation). Returns
-// FIM_ERR_UNSUPPORTED when this launch would need more workspace than `capacity` bytes.
+// FIM_ERR_UNSUPPORTED when this launch would need more workspace than `capacity` bytes. With
+// `launch` false it only answers that question (FIM_OK: it fits) and launches nothing.
 template <int DT, int SHAPE, int W, int OG, int KS>
-fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
+fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream, bool launch) {
     auto fn = tile_median_kernel<DT, SHAPE, W, OG, KS, 0>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -73,6 +74,7 @@ fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, 
     p.ntiles = (int)tiles;
     const int grid = (int)std::min<long long>(tiles, (long long)occ * device_sm_count());
     if (256 + (unsigned long long)grid * (unsigned long long)p.scratch_per_cta > capacity) return FIM_ERR_UNSUPPORTED;
+    if (!launch) return FIM_OK;
     p.scratch = scratch;
     if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;  // tile queue counter
     fn<<<grid, p.threads, p.smem_bytes, stream>>>(p);
@@ -81,10 +83,10 @@ fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, 
 }
 
 template <int DT, int SHAPE, int KS>
-fim_status launch_w_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
-    if (p.wide) return launch_typed_fixed<DT, SHAPE, 1, 1, KS>(p, scratch, capacity, stream);
-    return p.loc_om < 0 ? launch_typed_fixed<DT, SHAPE, 0, 1, KS>(p, scratch, capacity, stream)
-                        : launch_typed_fixed<DT, SHAPE, 0, 0, KS>(p, scratch, capacity, stream);
+fim_status launch_w_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream, bool launch) {
+    if (p.wide) return launch_typed_fixed<DT, SHAPE, 1, 1, KS>(p, scratch, capacity, stream, launch);
+    return p.loc_om < 0 ? launch_typed_fixed<DT, SHAPE, 0, 1, KS>(p, scratch, capacity, stream, launch)
+                        : launch_typed_fixed<DT, SHAPE, 0, 0, KS>(p, scratch, capacity, stream, launch);
 }
 
 template <int DT, int SHAPE, int KS, int XT>
@@ -113,18 +115,19 @@ fim_status launch_tile_kernel_ks(Plan& p, cudaStream_t stream) {
 }
 
 template <int KS>
-fim_status launch_tile_kernel_fixed_ks(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream) {
+fim_status launch_tile_kernel_fixed_ks(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream,
+                                       bool launch) {
     const bool disk = p.shape == kShapeDisk;
     switch (p.dtype) {
         case FIM_U8:
-            return disk ? launch_w_fixed<FIM_U8, kShapeDisk, KS>(p, scratch, capacity, stream)
-                        : launch_w_fixed<FIM_U8, kShapeSpans, KS>(p, scratch, capacity, stream);
+            return disk ? launch_w_fixed<FIM_U8, kShapeDisk, KS>(p, scratch, capacity, stream, launch)
+                        : launch_w_fixed<FIM_U8, kShapeSpans, KS>(p, scratch, capacity, stream, launch);
         case FIM_U16:
-            return disk ? launch_w_fixed<FIM_U16, kShapeDisk, KS>(p, scratch, capacity, stream)
-                        : launch_w_fixed<FIM_U16, kShapeSpans, KS>(p, scratch, capacity, stream);
+            return disk ? launch_w_fixed<FIM_U16, kShapeDisk, KS>(p, scratch, capacity, stream, launch)
+                        : launch_w_fixed<FIM_U16, kShapeSpans, KS>(p, scratch, capacity, stream, launch);
         case FIM_F32:
-            return disk ? launch_w_fixed<FIM_F32, kShapeDisk, KS>(p, scratch, capacity, stream)
-                        : launch_w_fixed<FIM_F32, kShapeSpans, KS>(p, scratch, capacity, stream);
+            return disk ? launch_w_fixed<FIM_F32, kShapeDisk, KS>(p, scratch, capacity, stream, launch)
+                        : launch_w_fixed<FIM_F32, kShapeSpans, KS>(p, scratch, capacity, stream, launch);
     }
     return FIM_ERR_INVALID_ARG;
 }

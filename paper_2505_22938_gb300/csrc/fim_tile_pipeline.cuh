@@ -132,10 +132,18 @@ struct Grp {
     }
 };
 
-// Diagnostics: thread 0 records clock64() at phase boundaries when a buffer is attached.
+// Diagnostics: thread 0 records clock64() at phase boundaries when a buffer is attached. The
+// stamps collect in the group's scan scratch (words 48..63, which no phase uses) and go to the
+// buffer together at the end of the tile, so that no stamp waits behind the tile's own global
+// stores.
 __device__ __forceinline__ void stamp(const Plan& P, int tile, int phase, const Grp& G) {
-    if (P.phase_clock != nullptr && G.tid == 0 && tile < P.phase_tiles)
-        P.phase_clock[tile * 8 + phase] = clock64();
+    if (P.phase_clock != nullptr && G.tid == 0 && tile < P.phase_tiles) {
+        extern __shared__ __align__(16) unsigned char smem_base[];
+        unsigned long long* st = reinterpret_cast<unsigned long long*>(smem_base + G.shift + P.off_misc + 48 * 4);
+        st[phase] = clock64();
+        if (phase == 7)
+            for (int i = 0; i < 8; ++i) P.phase_clock[tile * 8 + i] = st[i];
+    }
 }
 
 __device__ __forceinline__ int span_lo(int s) { return (int)(int16_t)(s & 0xffff); }
@@ -431,14 +439,25 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
     for (int i = tid * 4; i < nwords; i += P.threads * 4)
         *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
     G.sync();
+    // A warp takes one footprint row at a time; each lane loads up to kLoads pixels of it (all in
+    // flight at once) before it issues their shared-memory atomics.
+    constexpr int kLoads = 8;
     for (int v = warp; v < SH; v += nwarps) {
         const int fr = frow[v];
-        for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
-            const uint32_t key = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
-            if (k16)
-                atomicAdd(&bins[key >> 1], 1u << ((key & 1u) << 4));
-            else
-                atomicAdd(&bins[key], 1u);
+        const int hi = span_hi(fr);
+        for (int u0 = span_lo(fr) + lane; u0 <= hi; u0 += 32 * kLoads) {
+            uint32_t key[kLoads];
+#pragma unroll
+            for (int k = 0; k < kLoads; ++k)
+                key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v)) : 0u;
+#pragma unroll
+            for (int k = 0; k < kLoads; ++k) {
+                if (u0 + 32 * k > hi) break;
+                if (k16)
+                    atomicAdd(&bins[key[k] >> 1], 1u << ((key[k] & 1u) << 4));
+                else
+                    atomicAdd(&bins[key[k]], 1u);
+            }
         }
     }
     G.sync();
@@ -468,32 +487,41 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
     }
     for (int v = warp; v < SH; v += nwarps) {
         const int fr = frow[v];
-        for (int u = span_lo(fr) + lane; u <= span_hi(fr); u += 32) {
-            const uint32_t key = Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
-            uint32_t o;
-            if (k16) {
-                const uint32_t sh = (key & 1u) << 4;
-                o = (atomicAdd(&bins[key >> 1], 1u << sh) >> sh) & 0xffffu;
-            } else {
-                o = atomicAdd(&bins[key], 1u);
+        const int hi = span_hi(fr);
+        for (int u0 = span_lo(fr) + lane; u0 <= hi; u0 += 32 * kLoads) {
+            uint32_t key[kLoads];
+#pragma unroll
+            for (int k = 0; k < kLoads; ++k)
+                key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v)) : 0u;
+#pragma unroll
+            for (int k = 0; k < kLoads; ++k) {
+                if (u0 + 32 * k > hi) break;
+                uint32_t o;
+                if (k16) {
+                    const uint32_t sh = (key[k] & 1u) << 4;
+                    o = (atomicAdd(&bins[key[k] >> 1], 1u << sh) >> sh) & 0xffffu;
+                } else {
+                    o = atomicAdd(&bins[key[k]], 1u);
+                }
+                om[o] = Loc<W>::pack(u0 + 32 * k, v, cx0, cy0);
             }
-            om[o] = Loc<W>::pack(u, v, cx0, cy0);
         }
     }
 }
 
-// LSD radix ordinal transform: 8-bit passes over bounding-box positions, four for 32-bit
-// float keys, two for 16-bit data. Every pass after the first is stable; the first may order
-// equal digits arbitrarily (shared-memory atomics), since the later passes keep that order.
-// Each warp owns one contiguous segment of the current order; in a stable pass a pixel's new
-// place is its (digit, warp)-major exclusive offset plus its position among equal digits
-// earlier in the segment (warp match). Histograms are laid out warp-major with
-// a pad word so that the leaders of one warp never share a bank. The sorted positions end in
-// list B, which is then rewritten in place as the omnigram.
-template <int DT, int W>
+// LSD radix ordinal transform over bounding-box positions. Float keys in 1024-thread CTAs (C16):
+// a 65536-bin counting pass on the low 16 bits (Eq. 5's construction, like 16-bit data) followed
+// by two stable 8-bit passes on the high bytes; otherwise 8-bit passes only, four for 32-bit
+// float keys and two for 16-bit data. The first pass may order equal digits arbitrarily
+// (shared-memory atomics), since the later passes are stable. In a stable pass each warp owns one
+// contiguous segment of the current order, and a pixel's new place is its (digit, warp)-major
+// exclusive offset plus its position among equal digits earlier in the segment (warp match).
+// Histograms are laid out warp-major with a pad word so that the leaders of one warp never share
+// a bank. The sorted positions end in list B, which is then rewritten in place as the omnigram.
+template <int DT, int W, bool C16 = false>
 __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t* keys, typename Loc<W>::Pos* bufA,
-                                        typename Loc<W>::Pos* bufB, uint32_t* hist, uint32_t* wsum, int gx0, int gy0,
-                                        const Grp& G) {
+                                        typename Loc<W>::Pos* bufB, uint32_t* hist, uint32_t* wsum, uint32_t* bins,
+                                        int gx0, int gy0, const Grp& G) {
     using Pos = typename Loc<W>::Pos;
     const int tid = G.tid, lane = G.lane, warp = G.warp;
     const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
@@ -546,11 +574,17 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
         return u >= span_lo(fr) && u <= span_hi(fr);
     };
     // Pass 0, fused with the footprint load: every thread takes box positions tid, tid +
-    // nthreads, ... (coalesced rows), four loads in flight, and counts the low digit in its
-    // warp's histogram; equal digits may then land in any order (returned atomics), since the
-    // later passes are stable.
-    for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
-    __syncwarp();
+    // nthreads, ... (coalesced rows), four loads in flight, and counts the low digit (8 bits in its
+    // warp's histogram, or 16 bits in the block's packed bins); equal digits may then land in any
+    // order (returned atomics), since the later passes are stable.
+    if constexpr (C16) {
+        for (int i = tid * 4; i < 32768; i += nthreads * 4)
+            *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
+        G.sync();
+    } else {
+        for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
+        __syncwarp();
+    }
     for (int i0 = tid; i0 < area; i0 += 4 * nthreads) {
         uint32_t key[4];
         bool in[4];
@@ -568,27 +602,43 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
         for (int k = 0; k < 4; ++k)
             if (in[k]) {
                 keys[i0 + k * nthreads] = key[k];
-                atomicAdd(&hw[key[k] & 0xff], 1u);
+                if constexpr (C16)
+                    atomicAdd(&bins[(key[k] & 0xffffu) >> 1], 1u << ((key[k] & 1u) << 4));
+                else
+                    atomicAdd(&hw[key[k] & 0xff], 1u);
             }
     }
     G.sync();
-    scan_counts();
-    G.sync();
-    for (int i = tid; i < area; i += nthreads)
-        if (inside(i)) bufA[atomicAdd(&hw[keys[i] & 0xff], 1u)] = (Pos)i;
+    // the first pass's result goes to the list the stable passes start from: with C16 two stable
+    // passes follow (B -> A -> B), otherwise an odd number (A -> B -> ... -> B)
+    Pos* first = C16 ? bufB : bufA;
+    if constexpr (C16) {
+        scan_bins16(bins, wsum, P, G);
+        for (int i = tid; i < area; i += nthreads)
+            if (inside(i)) {
+                const uint32_t k = keys[i] & 0xffffu, sh = (k & 1u) << 4;
+                first[(atomicAdd(&bins[k >> 1], 1u << sh) >> sh) & 0xffffu] = (Pos)i;
+            }
+    } else {
+        scan_counts();
+        G.sync();
+        for (int i = tid; i < area; i += nthreads)
+            if (inside(i)) first[atomicAdd(&hw[keys[i] & 0xff], 1u)] = (Pos)i;
+    }
     G.sync();
     // stable passes over the current order: each warp owns one contiguous segment; a pixel's
     // new place is its (digit, warp)-major exclusive offset plus its position among equal
     // digits earlier in the segment (warp match)
-    const Pos* src = bufA;
-    Pos* dst = bufB;
-    constexpr int kPasses = DT == FIM_F32 ? 4 : 2;  // 8-bit digits of 32- or 16-bit keys
-    static_assert(kPasses % 2 == 0, "the sorted positions must end in list B");
+    const Pos* src = first;
+    Pos* dst = C16 ? bufA : bufB;
+    constexpr int kBits0 = C16 ? 16 : 8;                       // key bits the first pass sorted
+    constexpr int kPasses = (DT == FIM_F32 ? 32 - kBits0 : 16 - kBits0) / 8;  // stable 8-bit passes
+    static_assert(kPasses % 2 == (C16 ? 0 : 1), "the sorted positions must end in list B");
     const int N = P.N;
     const int seg = ((N + nwarps - 1) / nwarps + 31) & ~31;
     const int s0 = min(N, warp * seg), s1 = min(N, s0 + seg);
-    for (int pass = 1; pass < kPasses; ++pass) {
-        const int shift = 8 * pass;
+    for (int pass = 0; pass < kPasses; ++pass) {
+        const int shift = kBits0 + 8 * pass;
         for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
         __syncwarp();
         for (int i = s0 + lane; i < s1; i += 32)  // counts do not depend on the order
@@ -615,7 +665,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
         src = dst;
         dst = (dst == bufA) ? bufB : bufA;
     }
-    // an even number of passes: the sorted positions are in B; rewrite them in place as entries
+    // the sorted positions are in B; rewrite them in place as entries
     typename Loc<W>::E* om = reinterpret_cast<typename Loc<W>::E*>(bufB);
     for (int v = tid; v < N; v += nthreads) {
         const int pos = (int)bufB[v];
@@ -770,11 +820,24 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     stamp(P, tile, 1, G);
     // float data always takes the radix sort; 16-bit data takes it in small CTAs, where the
     // counting sort's 65536 bins would keep other CTAs off the SM
-    if (DT == FIM_F32 || (DT == FIM_U16 && P.sort == kSortRadix))
+    if constexpr (DT == FIM_F32) {
+        if (P.sort == kSortRadix16)
+            ordinal_transform_radix<DT, W, true>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
+                                                 place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
+                                                 place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
+                                                 reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc,
+                                                 reinterpret_cast<uint32_t*>(smem + P.loc_bins), gx0, gy0, G);
+        else
+            ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
+                                           place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
+                                           place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
+                                           reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, nullptr, gx0, gy0,
+                                           G);
+    } else if (DT == FIM_U16 && P.sort == kSortRadix)
         ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
                                        place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
                                        place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
-                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, gx0, gy0, G);
+                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, nullptr, gx0, gy0, G);
     else if constexpr (DT != FIM_F32)
         ordinal_transform_count<DT, W>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), misc, om, gx0, gy0,
                                        G);
@@ -1032,6 +1095,11 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         G.sync();
 
         // ---- 5. vertical sweeps: thread per window column, per-thread refinement ----------------
+        // ---- 6. output, fused: out = C[m], the input value at Omega[m] --------------------------
+        // Each sweep thread writes the pixels it solves (the downward threads also the seed row's
+        // pixel they start from). The gather of a pixel's value is issued right after its solve
+        // and its store waits for the next step, so the L2 latency of the scattered gathers hides
+        // behind the next slide instead of queueing at the end of the tile.
         stamp(P, tile, 5, G);
         if (warp < P.vthreads / 32) {
             const int groups = TX / 32;
@@ -1048,6 +1116,18 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             const int ncols = P.ncols;
             const int scan_groups = P.scan_groups;
             const int eoff = down ? 0 : -SP;
+            const Img im(P);
+            char* const out = static_cast<char*>(q == 0 ? P.out : P.outs[q]);
+            const int gx = tx0 + s;
+            V pval = V(0);       // value gathered for the last solved pixel, not yet stored
+            V* pdst = nullptr;   // where it goes (null: outside the image, or nothing pending)
+            auto gather = [&](int m, int tt) {
+                const uint32_t e = om[m];
+                pval = load_px<DT>(im, gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
+                const int gy = ty0 + tt;
+                pdst = (gx < im.w && gy < im.h) ? reinterpret_cast<V*>(out + (long long)gy * im.pitch) + gx : nullptr;
+            };
+            if (down) gather(p, t);  // the seed row's pixel
             for (int k = 0; k < steps; ++k) {
                 const uint16_t* ctr = ord + cv * SP + cu + eoff;
                 int d = 0;
@@ -1072,24 +1152,12 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                     thread_select<SHAPE, W, KS>(om, N, p, tp + d, tn, cu - cx0, cv - cy0, member, scan_groups);
                 if (mine < 0) set_status(FIM_ERR_INTERNAL);
                 p = max(mine, 0);
-                med[t * TX + s] = (uint16_t)p;
+                if (pdst) *pdst = pval;  // the previous pixel's value has arrived by now
+                gather(p, t);
             }
+            if (pdst) *pdst = pval;
         }
-        G.sync();
-
-        // ---- 6. output: the input value at Omega[m] ------------------------------------------------
-        stamp(P, tile, 6, G);
-        const Img im(P);
-        char* out = static_cast<char*>(q == 0 ? P.out : P.outs[q]);
-        const int txshift = P.txshift;
-        for (int idx = tid; idx < TX * TY; idx += nthreads) {
-            const int t = idx >> txshift, s = idx & (TX - 1);
-            const int gx = tx0 + s, gy = ty0 + t;
-            if (gx >= im.w || gy >= im.h) continue;
-            const uint32_t e = om[med[idx]];
-            const V val = load_px<DT>(im, gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
-            reinterpret_cast<V*>(out + (long long)gy * im.pitch)[gx] = val;
-        }
+        stamp(P, tile, 6, G);  // the first group thread's own sweep is done (output is fused into it)
         G.sync();
         stamp(P, tile, 7, G);
     }

@@ -125,3 +125,29 @@ def test_argument_checks_need_no_gpu():
     assert lib.fim_percentile_map(a, a + 2048, m, 18, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
     assert lib.fim_percentile_map(a, a + 2048, a + 2040, 16, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
     assert lib.fim_percentile_map(a, a + 2048, a + 2060, 16, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+
+
+def test_batch_rejects_aliased_images():
+    """One batch runs every job in one launch: an output overlapping its own input, another
+    job's input or another output is refused before any device work; a shared input is not."""
+    lib = fim.lib()
+    k = fim.fim_create_kernel_circle(2)
+    buf = ctypes.create_string_buffer(1 << 16)
+    a = ctypes.addressof(buf)
+
+    def create(jobs):
+        arr = (fim.fim_job * len(jobs))(*jobs)
+        h = ctypes.c_void_p()
+        return lib.fim_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(jobs), ctypes.byref(h))
+
+    def job(i, o):  # 8x8 u16 images, pitch 16 bytes: each spans 128 bytes
+        return fim.make_job(a + i, a + o, 8, 8, 16, fim.FIM_U16, k)
+
+    INVALID = 1
+    assert create([job(0, 64)]) == INVALID                      # own input and output overlap
+    assert create([job(0, 1024), job(2048, 1100)]) == INVALID   # two outputs overlap
+    assert create([job(0, 1024), job(1024 + 64, 3000)]) == INVALID  # an input under another output
+    assert create([job(0, 1024), job(3000, 1024 + 127)]) == INVALID  # last byte of an output
+    # disjoint outputs, one shared input: passes the checks (fails later without a GPU)
+    assert create([job(0, 1024), job(0, 2048)]) != INVALID
+    assert create([job(0, 1024), job(512, 1152)]) != INVALID    # outputs back to back

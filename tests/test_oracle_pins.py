@@ -357,6 +357,59 @@ def test_config_kernel_counts():
     assert len(oracle.ellipse_offsets(80, 40)) == 10041
 
 
+def test_ellipse_rows_closed_form_and_orientation():
+    """Row dy of the ellipse with semi-axis a along x and b along y holds the dx with
+    dx^2 b^2 <= a^2 (b^2 - dy^2), i.e. |dx| <= isqrt(a^2 (b^2 - dy^2)) // b: 2 * that + 1
+    taps. The x extent is +-a and the y extent +-b, so a swapped (a, b) fails."""
+    for a, b in ((80, 40), (5, 2), (2, 5), (7, 7), (13, 4), (1, 9)):
+        off = oracle.ellipse_offsets(a, b)
+        assert off[:, 0].min() == -a and off[:, 0].max() == a, (a, b)
+        assert off[:, 1].min() == -b and off[:, 1].max() == b, (a, b)
+        for dy in range(-b, b + 1):
+            half = math.isqrt(a * a * (b * b - dy * dy)) // b
+            row = np.sort(off[off[:, 1] == dy, 0])
+            assert np.array_equal(row, np.arange(-half, half + 1)), (a, b, dy)
+        if a != b:
+            assert not np.array_equal(np.sort(off, axis=0), np.sort(oracle.ellipse_offsets(b, a), axis=0))
+
+
+def _pick_count(verts):
+    """Lattice points inside or on a polygon with integer vertices by Pick's theorem:
+    A = I + B/2 - 1, so I + B = A + B/2 + 1 (A by the shoelace formula, B = sum over the edges
+    of gcd(|dx|, |dy|))."""
+    m = len(verts)
+    twice_area = 0
+    boundary = 0
+    for i in range(m):
+        (x0, y0), (x1, y1) = verts[i], verts[(i + 1) % m]
+        twice_area += x0 * y1 - x1 * y0
+        boundary += math.gcd(abs(x1 - x0), abs(y1 - y0))
+    assert twice_area > 0, "counter-clockwise"
+    return (twice_area + boundary) // 2 + 1
+
+
+def test_polygon_counts_pick_theorem():
+    """Convex polygons with lattice vertices (triangles, a skew quadrilateral, an irregular
+    hexagon, a thin sliver): the rasteriser's point count equals Pick's theorem, every vertex
+    is included, and mirroring the polygon mirrors the point set."""
+    polys = [
+        [(0, 0), (7, 0), (0, 5)],
+        [(-3, -2), (4, -1), (1, 6)],
+        [(-5, -1), (2, -4), (6, 3), (-1, 5)],
+        [(-6, 0), (-3, -5), (3, -5), (6, 0), (3, 5), (-3, 5)],
+        [(-9, -1), (9, 0), (-9, 1)],
+        [(0, 0), (11, 3), (4, 8)],
+    ]
+    for verts in polys:
+        off = oracle.polygon_offsets(np.asarray(verts, dtype=np.float64))
+        assert len(off) == _pick_count(verts), verts
+        pts = {tuple(p) for p in off.tolist()}
+        assert all(tuple(v) in pts for v in verts)
+        mirrored = [(-x, y) for x, y in reversed(verts)]  # mirrored in x, still counter-clockwise
+        moff = oracle.polygon_offsets(np.asarray(mirrored, dtype=np.float64))
+        assert {(-x, y) for x, y in moff.tolist()} == pts
+
+
 def test_fig4_ordinal_example():
     """Fig. 4: ties get consecutive ordinals, and a window's median value and median ordinal
     correspond through the reverse map."""
