@@ -169,6 +169,8 @@ int device_smem_limit() {
 static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 fim_status layout_plan(Plan* p, int smem_limit, bool stage_model = false);
 
+static int span_lo_host(int s) { return (int)(int16_t)(s & 0xffff); }
+
 static int elem_size(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); }
 
 fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, int smem_limit,
@@ -213,8 +215,6 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     p->S = ts.Tx + (k->xmax - k->xmin);
     p->SH = ts.Ty + (k->ymax - k->ymin);
     if (p->S > kMaxSide || p->SH > kMaxSide) return FIM_ERR_UNSUPPORTED;
-    // 8-bit coordinates need one axis that never reaches -128, which marks the padding entries
-    p->wide = (p->S > 256 || p->SH > 256 || (p->S == 256 && p->SH == 256)) ? 1 : 0;
     p->SP = (p->S + 1) & ~1;
     if ((p->SP / 2) % 2 == 0) p->SP += 2;  // odd number of 32-bit words per row: no bank aliasing
     p->tiles_x = (w + ts.Tx - 1) / ts.Tx;
@@ -235,6 +235,11 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     }
     if (N > 65535) return FIM_ERR_UNSUPPORTED;
     p->N = (int)N;
+    // 8-bit coordinates (u - S/2, v - SH/2) reach (-128, -128), the mark of the padding entries,
+    // only at box position (0, 0) of a 256 x 256 box; they serve unless that corner belongs to the
+    // footprint (then it would be a real entry, and a member of some window).
+    const bool corner = span_lo_host(p->frow[0]) == 0;
+    p->wide = (p->S > 256 || p->SH > 256 || (p->S == 256 && p->SH == 256 && corner)) ? 1 : 0;
     p->cx0 = S / 2;
     p->cy0 = p->SH / 2;
     p->div_magic = (unsigned)(((1ull << 32) + (unsigned)S - 1) / (unsigned)S);

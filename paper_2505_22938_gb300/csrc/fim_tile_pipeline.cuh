@@ -255,6 +255,67 @@ __device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, in
     return -1;
 }
 
+// Warp-cooperative exact selection for long walks (learned seeds): the same contract as
+// ballot_select, but every lane tests one aligned 128-bit group of entries per iteration, so a
+// warp covers 32 groups (256 entries of 16 bits) per step; a warp prefix sum of the per-lane
+// member counts finds the group holding the target, and the lane that owns it picks the entry.
+// Entries past N up to the last group are sentinels, never members; groups outside the omnigram
+// count nothing. The loop is bounded by the omnigram length.
+template <int SHAPE, int W>
+__device__ __forceinline__ int wide_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
+                                           int target, int px, int py, const Member<SHAPE, W>& member) {
+    constexpr int G = Loc<W>::kGroup;
+    constexpr int kShift = G == 8 ? 3 : 2;
+    constexpr int kb = G / 4;  // entries per 32-bit word
+    constexpr uint32_t kAll = (1u << G) - 1;
+    const int lane = threadIdx.x & 31;
+    WordTest<SHAPE, W> wt;
+    wt.init(member, px, py);
+    const uint4* om128 = reinterpret_cast<const uint4*>(om);
+    const bool up = c <= target;
+    int need = up ? target - c + 1 : c - target;
+    const int v0 = up ? p : p - 1;  // first entry to examine
+    const int glast = (N - 1) >> kShift;
+    const int g0 = v0 >> kShift;    // -1 below entry 0
+    const int o0 = v0 & (G - 1);
+    const uint32_t first = up ? (kAll << o0) & kAll : kAll >> (G - 1 - o0);
+    for (int it = 0; it * 32 <= glast + 1; ++it) {
+        const int g = up ? g0 + 32 * it + lane : g0 - 32 * it - lane;
+        uint32_t mk = 0;
+        if ((unsigned)g <= (unsigned)glast) {
+            const uint4 q = om128[g];
+            mk = wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb));
+            if (it == 0 && lane == 0) mk &= first;
+        }
+        const int cnt = __popc(mk);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t hit = __ballot_sync(kFull, incl >= need);
+        if (hit) {
+            const int j = __ffs(hit) - 1;
+            int m = 0;
+            if (lane == j) {
+                int k = need - (incl - cnt);  // the k-th member of this group, counted along the walk
+                uint32_t mask = mk;
+                if (up) {
+                    for (; k > 1; --k) mask &= mask - 1;
+                    m = G * g + __ffs(mask) - 1;
+                } else {
+                    for (; k > 1; --k) mask ^= 1u << (31 - __clz(mask));
+                    m = G * g + 31 - __clz(mask);
+                }
+            }
+            return __shfl_sync(kFull, m, j);
+        }
+        need -= __shfl_sync(kFull, incl, 31);
+        if (up ? g0 + 32 * (it + 1) > glast : g0 - 32 * (it + 1) < 0) break;
+    }
+    return -1;
+}
+
 // Per-thread exact selection (vertical sweep): every lane refines its own window. It scans the
 // omnigram from its pivot in aligned groups of entries (one 128-bit load), K groups per step
 // (the loop's votes and bookkeeping are paid once per K groups: K = 4 where scans are short,
@@ -901,9 +962,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         if (learned) {
             // Learned bracket (extension): the bracket MLP runs block-wide over a chunk of seeds
             // (thread per (seed, hidden unit), activations in the seed-histogram buffers), then one
-            // warp per seed counts its window at the bracket ends, histograms the ranks inside the
-            // bracket finely, and scans Omega from the fine bin of the target (or, on a miss, from
-            // the bracket end the target lies beyond).
+            // warp per seed counts its window at the bracket ends and at the predicted median, and
+            // walks Omega 256 entries per step from the prediction (or, on a miss, from the
+            // bracket end the target lies beyond). It replaces the plain seeds' histogram, whose
+            // one shared-memory atomic per window pixel is what makes them expensive.
             const uint16_t* wts =
                 P.off_model >= 0 ? reinterpret_cast<const uint16_t*>(smem_base + P.off_model) : P.model;
             const int chunk_max = min(nwarps, nseeds);
@@ -945,7 +1007,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                     h2[idx] = fmaxf(h, 0.f);
                 }
                 G.sync();
-                int lo = 0, hi = 0;
+                int lo = 0, hi = 0, pmid = 0;
                 if (warp < chunk) {  // output layer: lanes hold hidden units lane and lane + 32
                     const float x0 = h2[warp * kHidden + lane], x1 = h2[warp * kHidden + lane + 32];
                     float o0 = bf16_to_f32(wts[kOffW3 + lane * 2]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2]) * x1;
@@ -960,33 +1022,29 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                     const float span = (float)(hif - lof);
                     lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
                     hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
+                    pmid = clampi(__float2int_rn(lof + o0 * span), lo, hi);
                 }
-                G.sync();  // the histograms below overwrite the activations
+                G.sync();  // the activation buffers are reused by the next chunk
                 if (warp < chunk) {
                     const int sd = c0 + warp;
                     const int band = sd / P.G, g = sd % P.G;
                     const int s = g * GW + GW / 2, t = band * BH + BH / 2;
                     const int cu = s - xmin, cv = t - ymin;
-                    // One pass counts the window below lo and at or below hi and histograms the ranks
-                    // inside [lo, hi] in kFineBins fine bins. Every pixel makes one atomic: pixels
-                    // outside the bracket add to a lane-private spare word (its own bank), so the
-                    // bracket's few pixels are the only ones that can collide.
-                    constexpr int kFineBins = kSeedBins - 32;
-                    int hb = 0;
-                    while (((hi - lo) >> hb) >= kFineBins) ++hb;
-                    uint32_t* hw = shist + warp * kSeedBins;
-                    for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
-                    __syncwarp();
-                    int clo = 0, chi = 0;
+                    // One pass counts the window's ranks below the bracket's low end, below the
+                    // predicted median and up to the high end: compares and adds only, no
+                    // histogram and no atomics. The walk then starts at the prediction (a hit) or
+                    // at the bracket end the target lies beyond (a miss), so its length is the
+                    // prediction's error, whatever it is: the output stays exact.
+                    const int mid = clampi(pmid, lo, hi);
+                    int clo = 0, cmid = 0, chi = 0;
                     window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
                         clo += r < lo;
+                        cmid += r < mid;
                         chi += r <= hi;
-                        const bool in = (unsigned)(r - lo) <= (unsigned)(hi - lo);
-                        atomicAdd(&hw[in ? (r - lo) >> hb : kFineBins + lane], 1u);
                     });
                     clo = __reduce_add_sync(kFull, clo);
+                    cmid = __reduce_add_sync(kFull, cmid);
                     chi = __reduce_add_sync(kFull, chi);
-                    __syncwarp();
                     int pivot, below, kind;
                     if (target < clo) {         // below the bracket: walk down from lo
                         pivot = lo;
@@ -996,11 +1054,12 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                         pivot = hi + 1;
                         below = chi;
                         kind = 3;
-                    } else {                    // inside: the fine bin holding the target (the spare
-                        kind = 1;               // words come after every fine bin, so are not reached)
-                        pivot = lo + (hist_pick(hw, clo, target, &below) << hb);
+                    } else {                    // inside: walk from the predicted median
+                        pivot = mid;
+                        below = cmid;
+                        kind = 1;
                     }
-                    const int m = ballot_select(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+                    const int m = wide_select<SHAPE, W>(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
                     if (m < 0) set_status(FIM_ERR_INTERNAL);
                     if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
                     if (counting && lane == 0) {

@@ -103,6 +103,58 @@ def test_untrained_bracket_is_still_exact(dtype, r):
     assert st[0] > 0 and st[1] + st[2] + st[3] == st[0]
 
 
+def _train_on_photos(k, r, images=6, side=512):
+    """Training rows from the plain path's seed windows on photo-like images (labels: exact
+    medians), checked against the oracle on the first image; returns (rows tensor, count)."""
+    import torch
+    import paper_2505_22938_gb300 as fim
+    cap = 1 << 16
+    rows = torch.zeros((cap, ROW), dtype=torch.float32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for i in range(images):
+        img = datagen.config2_image(side, side, image_index=50 + i)
+        store, _ = to_device(img)
+        out = torch.empty_like(store)
+        fim.fim_collect_seed_samples(store.data_ptr(), out.data_ptr(), side, side, side * 2, fim.FIM_U16, k,
+                                     rows.data_ptr(), cap, count.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        if i == 0:
+            ys, xs = np.mgrid[0:side:37, 0:side:41]
+            assert np.array_equal(to_host(out)[ys, xs].ravel(),
+                                  oracle.median_points(img, oracle.disk_offsets(r), xs.ravel(), ys.ravel()))
+    n = int(count.item())
+    return rows[:n], n
+
+
+def test_trained_network_shortens_the_walk():
+    """What the trained network gains over the same exact seed solve without it: a constant
+    predictor (every seed's median guessed at the middle of the tile's feasible ranks, its bracket
+    calibrated on the same rows) against the network trained on photo-like seeds. Both give the
+    oracle's bytes; the network walks fewer omnigram ranks per seed."""
+    import paper_2505_22938_gb300 as fim
+    r = 48
+    k = fim.fim_create_kernel_circle(r)
+    data, n = _train_on_photos(k, r, images=8)
+    assert n > 500
+    trained = fim.Model.create(seed=1)
+    trained.train(data.data_ptr(), n, 40, 512, 2e-3)
+    trained.calibrate(data.data_ptr(), n, 0.9)
+    const = fim.Model.create(seed=1)
+    w = np.zeros(fim.Model.param_count(), np.float32)
+    w[-2:] = [0.5, np.log(0.25)]  # output bias: mu = middle of the feasible ranks, log sigma
+    const.set_params(w)
+    const.calibrate(data.data_ptr(), n, 0.9)
+    img = datagen.config2_image(384, 320, image_index=98)
+    exp = oracle.median_filter(img, oracle.disk_offsets(r))
+    got_t, st_t = _learned(img, k, trained)
+    got_c, st_c = _learned(img, k, const)
+    assert_bit_exact(got_t, exp, "trained network")
+    assert_bit_exact(got_c, exp, "constant predictor")
+    walk_t = st_t[4] / st_t[0]
+    walk_c = st_c[4] / st_c[0]
+    assert walk_t < 0.8 * walk_c, (walk_t, walk_c)
+
+
 def test_trained_bracket_exact_and_hits():
     """Train on seeds of a few photo-like images, then filter a new one: same bytes as the plain
     path, and most seed windows land inside the predicted bracket."""
