@@ -174,17 +174,18 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
                            fim_dtype dtype, const fim_kernel* k, fim_border border, void* stream);
 
 /*
- * Tunes the tile configuration for (current device, dtype, kernel geometry): every valid
- * configuration is run on this image (in -> out, which ends up holding the filtered image) and
- * timed with CUDA events; the fastest is kept in a process-wide cache that later fim_median,
- * fim_percentile and batch calls with the same dtype and kernel geometry use (a batch runs a
- * job's tile groups side by side in 1024-thread CTAs, so the single-image choice carries over).
+ * Tunes the tile configuration for (current device, dtype, kernel geometry, image-size class):
+ * every valid configuration is run on this image (in -> out, which ends up holding the filtered
+ * image) and timed with CUDA events; the fastest is kept in a process-wide cache that later
+ * fim_median, fim_percentile and related calls with the same dtype, kernel geometry and size
+ * class use. Size classes: up to 1, 4 and 16 Mpix, and larger. Batches take the largest
+ * class (the tiles of all their jobs share one queue, so they fill the GPU like a large image).
  * cta_threads = 0 tunes over all CTA sizes; 256, 512 or 1024 restricts the search to that CTA
  * size and stores the result separately, for callers that plan with a fixed CTA size.
  * If the environment variable FIM_TUNE_CACHE names a file, the cache is loaded from it on first
  * use and rewritten after each tuning. tile_w / tile_h (may be NULL) receive the chosen tile.
- * The choice depends on the image size: tune on an image of the size that will be filtered
- * (shapes tuned on a 512x512 crop slowed 4096x4096 images at r = 8-48 by up to 30 %).
+ * The choice depends on the image size (shapes tuned on a 512x512 crop slowed 4096x4096 images at
+ * r = 8-48 by up to 30 %), hence the size classes.
  * Synchronous. Not part of the paper: its GPU tiling is fixed by radius (Sec. 4.2).
  */
 fim_status fim_autotune(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,

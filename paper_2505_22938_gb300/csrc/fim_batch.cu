@@ -1,14 +1,17 @@
-// Batched persistent launch (host side): many images of any size, dtype and kernel in one
-// kernel launch. The batch object owns its device-side plans (sorted by decreasing cost per
-// tile) and its workspace, whose header holds one tile counter per job; fim_batch_run() only
-// zeroes the header and launches: both are stream operations and can be captured in a CUDA
-// graph.
+// Batched persistent launch (host side): many images of any size, dtype and kernel. The jobs are
+// grouped into classes that share a tile-pipeline instantiation and CTA size; each class runs as
+// one persistent kernel whose device-side queue spans the tiles of all its jobs (sorted by
+// decreasing cost per tile), and the class kernels run side by side on forked streams, so the
+// tail of one class overlaps the others. The batch object owns its device-side plans, queues and
+// workspace and its side streams; fim_batch_run() only zeroes the queue counters and launches,
+// all stream operations, so a run can be captured in a CUDA graph.
 #include <string.h>
 
 #include <algorithm>
 #include <iterator>
 #include <new>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "fim_internal.h"
@@ -17,11 +20,15 @@ using namespace fim;
 
 struct fim_batch {
     int njobs = 0;
-    int total_tiles = 0, max_groups = 1, header_bytes = 256;
-    int grid = 0, threads = 0, smem = 0;
-    long long scratch_per_cta = 0;
-    Plan* d_plans = nullptr;
-    unsigned char* scratch = nullptr;
+    int total_tiles = 0;
+    std::vector<BatchClass> classes;          // in launch order (largest estimated cost first)
+    std::vector<BatchClassArgs> args;         // one per class
+    Plan* d_plans = nullptr;                  // every plan, grouped by class
+    int* d_tile_start = nullptr;              // per class, its jobs' tile prefix sums
+    unsigned int* d_counters = nullptr;       // one queue counter per class
+    unsigned char* scratch = nullptr;         // per class, grid * scratch_per_cta bytes
+    std::vector<cudaStream_t> side;           // classes after the first run on these
+    std::vector<cudaEvent_t> ev;              // fork event, then one join event per side stream
     int device = 0;
 };
 
@@ -70,8 +77,16 @@ void free_batch(fim_batch* b) {
     if (!b) return;
     cudaDeviceSynchronize();
     if (b->d_plans) cudaFree(b->d_plans);
+    if (b->d_tile_start) cudaFree(b->d_tile_start);
+    if (b->d_counters) cudaFree(b->d_counters);
     if (b->scratch) cudaFree(b->scratch);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     delete b;
+}
+
+fim_status class_kernel(const BatchClass& c, const BatchClassArgs* a, int* occ, cudaStream_t st) {
+    return c.ks == 4 ? batch_class_k4(c, a, occ, st) : batch_class_k8(c, a, occ, st);
 }
 
 }  // namespace
@@ -81,7 +96,6 @@ extern "C" {
 fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
     if (!out || !jobs || count <= 0) return FIM_ERR_INVALID_ARG;
     *out = nullptr;
-    constexpr int kCta = 1024;  // every batch CTA; jobs with smaller configurations run several groups
     std::vector<Plan> plans((size_t)count);
     for (int i = 0; i < count; ++i) {
         const fim_job& j = jobs[i];
@@ -97,7 +111,8 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
     for (int i = 0; i < count; ++i) {
         const fim_job& j = jobs[i];
         TileShape ts;
-        fim_status s = choose_tile(j.kernel, j.dtype, limit, &ts);
+        // a batch fills the GPU with the tiles of all its jobs: the shapes tuned for large images
+        fim_status s = choose_tile(j.kernel, j.dtype, limit, &ts, 0, 0);
         if (s != FIM_OK) return s;
         const int n = j.kernel->n;
         int rank = (n - 1) / 2;
@@ -109,26 +124,48 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
         p.out = j.out;
         p.pitch = (long long)j.pitch_bytes;
         p.ntiles = p.tiles_x * p.tiles_y;
-        // as many groups as fit the CTA and shared memory, but no more than the job has tiles
-        int groups = std::min(kCta / p.threads, kMaxBatchGroups);
-        while (groups > 1 && p.tab_bytes + (size_t)groups * p.group_bytes > (size_t)limit) --groups;
-        p.groups = std::max(1, std::min(groups, p.ntiles));
     }
+    // classes: the instantiation a plan runs on and its CTA size
+    auto key = [&](const Plan& p) {
+        return std::make_tuple(p.dtype, p.shape, p.wide, p.loc_om < 0 ? 1 : 0, p.scan_groups == 4 ? 4 : 8, p.threads);
+    };
     std::vector<int> order((size_t)count);
     std::iota(order.begin(), order.end(), 0);
-    // the CTAs visit the jobs in this order: expensive tiles first, cheap ones fill the tail
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return tile_cost(plans[a]) > tile_cost(plans[b]); });
+    // grouped by class; inside a class the CTAs start on the expensive tiles, cheap ones fill the tail
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (key(plans[a]) != key(plans[b])) return key(plans[a]) < key(plans[b]);
+        return tile_cost(plans[a]) > tile_cost(plans[b]);
+    });
     std::vector<Plan> sorted((size_t)count);
-    long long tiles = 0, spc = 0;
-    int smem = 0, max_groups = 1;
+    std::vector<int> tile_start((size_t)count);
+    std::vector<BatchClass> classes;
+    std::vector<int> first_job;  // per class, its first plan in `sorted`
+    std::vector<double> cost;    // per class, estimated total cost
+    long long tiles = 0;
     for (int i = 0; i < count; ++i) {
-        Plan& p = sorted[i];
-        p = plans[order[i]];
+        const Plan& p = plans[order[i]];
+        sorted[i] = p;
+        if (i == 0 || key(p) != key(plans[order[i - 1]])) {
+            BatchClass c{};
+            c.dtype = p.dtype;
+            c.shape = p.shape;
+            c.wide = p.wide;
+            c.og = p.loc_om < 0 ? 1 : 0;
+            c.ks = p.scan_groups == 4 ? 4 : 8;
+            c.threads = p.threads;
+            classes.push_back(c);
+            first_job.push_back(i);
+            cost.push_back(0.0);
+        }
+        BatchClass& c = classes.back();
+        tile_start[i] = c.total_tiles;
+        if ((long long)c.total_tiles + p.ntiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
+        c.total_tiles += p.ntiles;
+        c.njobs += 1;
+        c.smem = std::max(c.smem, p.smem_bytes);
+        c.scratch_per_cta = std::max(c.scratch_per_cta, p.scratch_per_cta);
+        cost.back() += tile_cost(p) * p.ntiles;
         tiles += p.ntiles;
-        spc = std::max(spc, p.scratch_per_cta);
-        smem = std::max(smem, p.tab_bytes + p.groups * p.group_bytes);
-        max_groups = std::max(max_groups, p.groups);
     }
     if (tiles > 0x7fffffffLL) return FIM_ERR_UNSUPPORTED;
     fim_batch* b = new (std::nothrow) fim_batch();
@@ -136,27 +173,68 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
     cudaGetDevice(&b->device);
     b->njobs = count;
     b->total_tiles = (int)tiles;
-    b->max_groups = max_groups;
-    b->scratch_per_cta = spc;
-    b->threads = kCta;
-    b->smem = smem;
-    b->header_bytes = (int)((((size_t)count * 4) + 255) & ~(size_t)255);
-    fim_status s = batch_prepare(smem);
-    if (s == FIM_OK) s = batch_grid(b->threads, b->smem, tiles, &b->grid);
-    if (s != FIM_OK) {
-        free_batch(b);
-        return s;
+    const int ncls = (int)classes.size();
+    size_t scratch_bytes = 0;
+    std::vector<size_t> scratch_off((size_t)ncls);
+    for (int c = 0; c < ncls; ++c) {
+        BatchClass& k = classes[c];
+        int occ = 0;
+        fim_status s = class_kernel(k, nullptr, &occ, nullptr);
+        if (s != FIM_OK) {
+            free_batch(b);
+            return s;
+        }
+        k.grid = (int)std::min<long long>(k.total_tiles, (long long)occ * device_sm_count());
+        scratch_off[c] = scratch_bytes;
+        scratch_bytes += ((size_t)k.grid * (size_t)k.scratch_per_cta + 255) & ~(size_t)255;
     }
-    const size_t scratch_bytes = (size_t)b->header_bytes + (size_t)b->grid * (size_t)max_groups * (size_t)spc;
     if (cudaMalloc(&b->d_plans, sizeof(Plan) * (size_t)count) != cudaSuccess ||
-        cudaMalloc(&b->scratch, scratch_bytes) != cudaSuccess) {
+        cudaMalloc(&b->d_tile_start, sizeof(int) * (size_t)count) != cudaSuccess ||
+        cudaMalloc(&b->d_counters, 256 * (size_t)ncls) != cudaSuccess ||
+        (scratch_bytes > 0 && cudaMalloc(&b->scratch, scratch_bytes) != cudaSuccess)) {
         cudaGetLastError();
         free_batch(b);
         return FIM_ERR_OOM;
     }
-    if (cudaMemcpy(b->d_plans, sorted.data(), sizeof(Plan) * (size_t)count, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(b->d_plans, sorted.data(), sizeof(Plan) * (size_t)count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_tile_start, tile_start.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
         free_batch(b);
         return FIM_ERR_CUDA;
+    }
+    // launch order: the classes with the most work first, so that the small ones fill the tail
+    std::vector<int> lorder((size_t)ncls);
+    std::iota(lorder.begin(), lorder.end(), 0);
+    std::stable_sort(lorder.begin(), lorder.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    for (int c : lorder) {
+        const BatchClass& k = classes[c];
+        BatchClassArgs a;
+        a.plans = b->d_plans + first_job[c];
+        a.tile_start = b->d_tile_start + first_job[c];
+        a.njobs = k.njobs;
+        a.total_tiles = k.total_tiles;
+        a.counter = reinterpret_cast<unsigned int*>(reinterpret_cast<unsigned char*>(b->d_counters) +
+                                                    256 * b->classes.size());
+        a.scratch = b->scratch ? b->scratch + scratch_off[c] : nullptr;
+        a.scratch_per_cta = k.scratch_per_cta;
+        b->classes.push_back(k);
+        b->args.push_back(a);
+    }
+    for (int c = 1; c < ncls; ++c) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            free_batch(b);
+            return FIM_ERR_CUDA;
+        }
+        b->side.push_back(st);
+    }
+    for (int e = 0; e < ncls; ++e) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            free_batch(b);
+            return FIM_ERR_CUDA;
+        }
+        b->ev.push_back(ev);
     }
     *out = b;
     return FIM_OK;
@@ -164,22 +242,36 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
 
 fim_status fim_batch_run(fim_batch* b, void* stream) {
     if (!b) return FIM_ERR_INVALID_ARG;
-    BatchArgs a;
-    a.plans = b->d_plans;
-    a.njobs = b->njobs;
-    a.header_bytes = b->header_bytes;
-    a.max_groups = b->max_groups;
-    a.scratch = b->scratch;
-    a.scratch_per_cta = b->scratch_per_cta;
-    return batch_launch(a, b->grid, b->threads, b->smem, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ncls = (int)b->classes.size();
+    if (cudaMemsetAsync(b->d_counters, 0, 256 * (size_t)ncls, st) != cudaSuccess) return FIM_ERR_CUDA;
+    // fork: the side streams wait for the counters, run their classes, and the caller's stream
+    // waits for all of them
+    if (ncls > 1 && cudaEventRecord(b->ev[0], st) != cudaSuccess) return FIM_ERR_CUDA;
+    for (int c = 0; c < ncls; ++c) {
+        cudaStream_t cs = c == 0 ? st : b->side[c - 1];
+        if (c > 0 && cudaStreamWaitEvent(cs, b->ev[0], 0) != cudaSuccess) return FIM_ERR_CUDA;
+        fim_status s = class_kernel(b->classes[c], &b->args[c], nullptr, cs);
+        if (s != FIM_OK) return s;
+        if (c > 0 && cudaEventRecord(b->ev[c], cs) != cudaSuccess) return FIM_ERR_CUDA;
+    }
+    for (int c = 1; c < ncls; ++c)
+        if (cudaStreamWaitEvent(st, b->ev[c], 0) != cudaSuccess) return FIM_ERR_CUDA;
+    return FIM_OK;
 }
 
 fim_status fim_batch_info(const fim_batch* b, int* total_tiles, int* grid, int* threads, int* smem_bytes) {
     if (!b) return FIM_ERR_INVALID_ARG;
+    int g = 0, t = 0, sm = 0;
+    for (const BatchClass& c : b->classes) {
+        g += c.grid;
+        t = std::max(t, c.threads);
+        sm = std::max(sm, c.smem);
+    }
     if (total_tiles) *total_tiles = b->total_tiles;
-    if (grid) *grid = b->grid;
-    if (threads) *threads = b->threads;
-    if (smem_bytes) *smem_bytes = b->smem;
+    if (grid) *grid = g;
+    if (threads) *threads = t;
+    if (smem_bytes) *smem_bytes = sm;
     return FIM_OK;
 }
 

@@ -246,6 +246,12 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     int hs = 0;
     while (((p->N - 1) >> hs) >= kSeedBins) ++hs;
     p->hist_shift = hs;
+    // Seeds: the omnigram walk reads about N/2 entries, the histogram n pixels with a shared-memory
+    // atomic each; the walk wins where the footprint is small against the kernel (measured on the
+    // 4096^2 photo-like workload: walk +1 % at r = 64, +8 % at r = 96; histogram ahead up to r = 48).
+    p->seed_mode = p->N < 4 * p->n ? kSeedWalk : kSeedHistogram;
+    if (const char* e = getenv("FIM_SEEDS"))  // experiments: 0 histogram, 1 walk, 2 count at the middle
+        if (*e >= '0' && *e <= '2' && e[1] == 0) p->seed_mode = *e - '0';
     for (int j = 0; j < p->ncols; ++j) {
         const int dx = k->xmin + j;
         p->vtab[2 * j] = k->ctop[j] * SP + dx;
@@ -272,7 +278,14 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
 
 fim_status plan_stage_model(Plan* p, int smem_limit) {
     if (p->model == nullptr) return FIM_OK;
-    if (layout_plan(p, smem_limit, true) == FIM_OK) return FIM_OK;
+    // Stage the parameters only where they fit beside everything the plain layout keeps in shared
+    // memory: moving the omnigram or a sort list to global memory costs far more than reading
+    // the parameters from global memory (measured: 3x the sort time at r = 64).
+    const int om = p->loc_om, keys = p->loc_keys, a = p->loc_a, b = p->loc_b;
+    if (layout_plan(p, smem_limit, true) == FIM_OK &&
+        (p->loc_om >= 0) == (om >= 0) && (p->loc_keys >= 0) == (keys >= 0) && (p->loc_a >= 0) == (a >= 0) &&
+        (p->loc_b >= 0) == (b >= 0))
+        return FIM_OK;
     return layout_plan(p, smem_limit, false);
 }
 
@@ -282,7 +295,10 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
     const size_t om_bytes = align16((size_t)p->N * omb);
     const size_t ord_bytes = align16((size_t)SP * p->SH * 2);
     const size_t med_bytes = align16((size_t)Tx * Ty * 2);
-    const size_t shist_bytes = (size_t)kSeedBins * std::min(p->nwarps, p->RB * p->G) * 4;
+    // one coarse histogram per concurrently solved seed; seeds that walk the omnigram need none
+    // (the learned seeds keep one histogram's room for the MLP's shared pre-activations)
+    const size_t shist_bytes =
+        (size_t)kSeedBins * (p->seed_mode == kSeedHistogram ? std::min(p->nwarps, p->RB * p->G) : 1) * 4;
     const size_t solve_bytes = ord_bytes + med_bytes + shist_bytes;
     size_t tab = 0;
     auto take_tab = [&](int* field, size_t bytes) {
@@ -391,7 +407,8 @@ static bool parse_tile_env(TileShape* ts) {
     return true;
 }
 
-fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int cta_threads) {
+fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int w, int h,
+                       int cta_threads) {
     static const TileShape cands[] = {{32, 32, 2, 1}, {32, 32, 4, 1}, {64, 128, 8, 2}, {64, 64, 8, 2},
                                       {32, 64, 8, 2}, {32, 32, 8, 2}, {32, 16, 8, 2}};
     TileShape forced;
@@ -408,7 +425,8 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     }
     TileShape tuned;
     // configuration chosen by fim_autotune: for this CTA size first, then for any size
-    if ((cta_threads > 0 && tuned_lookup(k, dtype, &tuned, cta_threads)) || tuned_lookup(k, dtype, &tuned, 0)) {
+    const int sc = size_class(w, h);
+    if ((cta_threads > 0 && tuned_lookup(k, dtype, &tuned, sc, cta_threads)) || tuned_lookup(k, dtype, &tuned, sc, 0)) {
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
         fim_status s = make_plan(k, dtype, 0, 1, 1, tuned, smem_limit, p);
@@ -522,7 +540,7 @@ fim_status filter_rank(const void* in, void* out, int w, int h, size_t pitch, in
     if (smem_limit < 0) smem_limit = device_smem_limit();
     if (smem_limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    fim_status s = choose_tile(k, dtype, smem_limit, &ts);
+    fim_status s = choose_tile(k, dtype, smem_limit, &ts, w, h);
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
@@ -693,7 +711,7 @@ fim_status fim_percentiles(const void* in, void* const* outs, const double* perc
     if (smem_limit < 0) smem_limit = device_smem_limit();
     if (smem_limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    fim_status s = choose_tile(k, dtype, smem_limit, &ts);
+    fim_status s = choose_tile(k, dtype, smem_limit, &ts, w, h);
     if (s != FIM_OK) return s;
     int ranks[kMaxRanks];
     for (int i = 0; i < count; ++i)
@@ -733,7 +751,7 @@ fim_status fim_percentile_map(const void* in, void* out, const float* percentile
     if (smem_limit < 0) smem_limit = device_smem_limit();
     if (smem_limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    s = choose_tile(k, dtype, smem_limit, &ts);
+    s = choose_tile(k, dtype, smem_limit, &ts, w, h);
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
@@ -787,7 +805,7 @@ fim_status fim_median_host(const void* in_host, void* out_host, int w, int h, si
     const int limit = device_smem_limit();
     if (limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    s = choose_tile(k, dtype, limit, &ts);
+    s = choose_tile(k, dtype, limit, &ts, w, h);
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
@@ -875,7 +893,7 @@ fim_status fim_plan_info(const fim_kernel* k, fim_dtype dtype, int w, int h, int
     const int limit = device_smem_limit();
     if (limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    fim_status s = choose_tile(k, dtype, limit, &ts);
+    fim_status s = choose_tile(k, dtype, limit, &ts, w, h);
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;

@@ -48,6 +48,15 @@ struct TileShape {
     int G;
 };
 
+// How the plain seed windows are solved (Sec. 4.2: seeds from histograms of the omnigram):
+//   kSeedHistogram - a coarse histogram of the window's ranks (shared-memory atomics), scanned to
+//                    the target's bin, then a ballot scan of the omnigram from that bin;
+//   kSeedWalk      - a walk of the omnigram from rank 0 (or from N) counting the window's members
+//                    512 entries a step, which is the histogram of the omnigram, bin by bin;
+//   kSeedMidCount  - the window's members below the middle of the feasible ranks counted in the
+//                    ordinal image, then the walk from there.
+enum SeedMode : int { kSeedHistogram = 0, kSeedWalk = 1, kSeedMidCount = 2 };
+
 enum SortKind : int {
     kSortCount8 = 0,   // 256-bin counting sort (8-bit data)
     kSortCount16 = 1,  // 65536-bin counting sort with packed 16-bit bins (16-bit data, Eq. 5)
@@ -88,6 +97,7 @@ struct Plan {
     int cx0, cy0;           // omnigram coordinates are stored as (u - cx0, v - cy0), int8 each
     unsigned div_magic;     // ceil(2^32 / S): v = umulhi(pos, magic) for pos < 2^16 (radix path)
     int hist_shift;         // seed histogram: bin = rank >> hist_shift
+    int seed_mode;          // SeedMode of the plain seeds
     int sort;               // SortKind
     int wide;               // 1: footprint box wider than 256: 32-bit omnigram entries and positions
     // learned rank bracket for the seed windows (all optional; null = the plain histogram seeds)
@@ -131,16 +141,24 @@ struct Plan {
 constexpr size_t kPlanScalarBytes = ((offsetof(Plan, frow) + 15) / 16) * 16;
 static_assert(offsetof(Plan, frow) % 4 == 0, "plan scalars are copied as 32-bit words");
 
-// Tile groups per batch CTA: each has its own named barrier, 1..15 (0 is the whole CTA).
-constexpr int kMaxBatchGroups = 15;
 
-// Arguments of the batched persistent launch (plans live in device memory).
-struct BatchArgs {
-    const Plan* plans;          // njobs plans, device memory, in the order the CTAs visit them
-    int njobs;
-    int header_bytes;           // scratch header: one tile counter per job (zeroed before launch)
-    int max_groups;             // group slots per CTA in the scratch layout
-    unsigned char* scratch;     // header + grid * max_groups * scratch_per_cta
+// One class of a batch: jobs whose plans run on the same tile-pipeline instantiation and CTA size.
+struct BatchClass {
+    int dtype, shape, wide, og, ks;  // instantiation: element type, kernel shape, omnigram encoding
+                                     // and home (global when og), scan groups per step (4 or 8)
+    int threads, smem;               // CTA size and dynamic shared memory (the largest of its plans)
+    int grid;                        // persistent CTAs
+    int njobs, total_tiles;
+    long long scratch_per_cta;       // the largest of its plans
+};
+
+// Arguments of one class kernel (all pointers are device memory owned by the batch).
+struct BatchClassArgs {
+    const Plan* plans;          // the class's plans, in the order of their tiles in the queue
+    const int* tile_start;      // njobs exclusive prefix sums of the plans' tile counts
+    int njobs, total_tiles;
+    unsigned int* counter;      // the class's tile queue (zeroed before each run)
+    unsigned char* scratch;     // grid * scratch_per_cta bytes of per-CTA buffers
     long long scratch_per_cta;
 };
 
@@ -167,12 +185,23 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
 // Re-lays out a plan whose model is set so that the bracket MLP's parameters are staged in
 // shared memory; keeps them in device memory (off_model = -1) when they do not fit.
 fim_status plan_stage_model(Plan* p, int smem_limit);
-fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int cta_threads = 0);
+// Tile shape for an image of w x h (w or h <= 0: a batch, which fills the GPU like a large image).
+fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int w, int h,
+                       int cta_threads = 0);
 int device_smem_limit();
 
 // Autotuner cache (fim_tune.cu).
-bool tuned_lookup(const fim_kernel* k, int dtype, TileShape* ts, int cta_threads = 0);
-void tuned_store(const fim_kernel* k, int dtype, const TileShape& ts, int cta_threads = 0);
+// Image-size classes of the autotuner cache: the best tile shape depends on how many tiles an
+// image has against the SMs. 0: up to 1 Mpix, 1: up to 4 Mpix, 2: up to 16 Mpix, 3: larger (and
+// batches, whose tiles of all jobs share one queue).
+constexpr int kSizeClasses = 4;
+inline int size_class(int w, int h) {
+    if (w <= 0 || h <= 0) return kSizeClasses - 1;
+    const long long px = (long long)w * h;
+    return px <= (1ll << 20) ? 0 : (px <= (1ll << 22) ? 1 : (px <= (1ll << 24) ? 2 : 3));
+}
+bool tuned_lookup(const fim_kernel* k, int dtype, TileShape* ts, int size_cls, int cta_threads = 0);
+void tuned_store(const fim_kernel* k, int dtype, const TileShape& ts, int size_cls, int cta_threads = 0);
 void tuned_clear();
 void tile_candidates(std::vector<TileShape>* out);
 
@@ -183,7 +212,7 @@ void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 // Device launch (fim_tile.cu).
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream);
 fim_status read_and_clear_device_status(cudaStream_t stream);
-fim_status read_and_clear_batch_status();  // (fim_batch_kernel.cu) called by the above after its sync
+
 // (fim_tile_k4.cu) the kernels with 4 omnigram groups per scan step, and their status word
 fim_status launch_tile_kernel_k4(Plan& p, cudaStream_t stream);
 fim_status launch_tile_kernel_fixed_k4(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream,
@@ -202,8 +231,12 @@ fim_status launch_percentile_ranks(const float* pct, long long pct_pitch, int w,
 // `launch` false, only that check (FIM_OK: it fits).
 fim_status launch_tile_kernel_fixed(Plan& p, unsigned char* scratch, size_t capacity, cudaStream_t stream,
                                     bool launch = true);
-fim_status batch_prepare(int smem);
-fim_status batch_grid(int threads, int smem, long long total_tiles, int* grid);
-fim_status batch_launch(const BatchArgs& a, int grid, int threads, int smem, cudaStream_t stream);
+// Batch class kernels (fim_batch_k8.cu / fim_batch_k4.cu, by c.ks): with a == nullptr, the set-up
+// of c's kernel (shared-memory opt-in) and its resident CTAs per SM in *occ; otherwise a launch of
+// c.grid CTAs on `stream`.
+fim_status batch_class_k8(const BatchClass& c, const BatchClassArgs* a, int* occ, cudaStream_t stream);
+fim_status batch_class_k4(const BatchClass& c, const BatchClassArgs* a, int* occ, cudaStream_t stream);
+fim_status read_and_clear_batch_k8_status();
+fim_status read_and_clear_batch_k4_status();
 
 }  // namespace fim

@@ -259,7 +259,7 @@ fim_status run_filter(const void* in, void* out, int w, int h, size_t pitch, int
     const int limit = device_smem_limit();
     if (limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    fim_status s = choose_tile(k, dtype, limit, &ts);
+    fim_status s = choose_tile(k, dtype, limit, &ts, w, h);
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;

@@ -22,10 +22,11 @@ fim_status read_and_clear_device_status(cudaStream_t stream) {
     // every translation unit with device code has its own status word: report the first error
     const fim_status a = read_and_clear_unit_status();
     const fim_status b = read_and_clear_k4_status();
-    const fim_status c = read_and_clear_batch_status();
+    const fim_status c = read_and_clear_batch_k8_status();
+    const fim_status c4 = read_and_clear_batch_k4_status();
     const fim_status d = read_and_clear_extras_status();
     const fim_status e = read_and_clear_map_status();
-    for (fim_status x : {a, b, c, d, e})
+    for (fim_status x : {a, b, c, c4, d, e})
         if (x != FIM_OK) return x;
     return FIM_OK;
 }

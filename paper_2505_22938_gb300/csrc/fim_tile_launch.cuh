@@ -132,14 +132,5 @@ fim_status launch_tile_kernel_fixed_ks(Plan& p, unsigned char* scratch, size_t c
     return FIM_ERR_INVALID_ARG;
 }
 
-// This translation unit's device status word (each unit that includes the pipeline has one).
-fim_status read_and_clear_unit_status() {
-    int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return FIM_ERR_CUDA;
-    const int zero = 0;
-    if (v != 0 && cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return FIM_ERR_CUDA;
-    return (fim_status)v;
-}
-
 }  // namespace
 }  // namespace fim

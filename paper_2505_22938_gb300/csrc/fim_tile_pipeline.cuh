@@ -114,6 +114,15 @@ __device__ __forceinline__ uint32_t lanemask_ge() {
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
 
+// This translation unit's device status word, read and cleared by the host.
+inline fim_status read_and_clear_unit_status() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return FIM_ERR_CUDA;
+    const int zero = 0;
+    if (v != 0 && cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return FIM_ERR_CUDA;
+    return (fim_status)v;
+}
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
 // A tile group: the threads that run one tile's pipeline. A CTA holds one group (single-image
@@ -255,12 +264,13 @@ __device__ __forceinline__ int ballot_select(const E* __restrict__ om, int N, in
     return -1;
 }
 
-// Warp-cooperative exact selection for long walks (learned seeds): the same contract as
-// ballot_select, but every lane tests one aligned 128-bit group of entries per iteration, so a
-// warp covers 32 groups (256 entries of 16 bits) per step; a warp prefix sum of the per-lane
-// member counts finds the group holding the target, and the lane that owns it picks the entry.
-// Entries past N up to the last group are sentinels, never members; groups outside the omnigram
-// count nothing. The loop is bounded by the omnigram length.
+// Warp-cooperative exact selection for long walks (seed windows): the same contract as
+// ballot_select, but every lane tests two consecutive aligned 128-bit groups of entries per
+// step, so a warp covers 64 groups (512 entries of 16 bits) per step. A warp reduction of the
+// per-lane member counts says whether the step holds the target; only that last step takes the
+// warp prefix sum that finds the lane, and the lane picks the entry. Entries past N up to the
+// last group are sentinels, never members; groups outside the omnigram count nothing. The loop is
+// bounded by the omnigram length.
 template <int SHAPE, int W>
 __device__ __forceinline__ int wide_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
                                            int target, int px, int py, const Member<SHAPE, W>& member) {
@@ -279,27 +289,35 @@ __device__ __forceinline__ int wide_select(const typename Loc<W>::E* __restrict_
     const int g0 = v0 >> kShift;    // -1 below entry 0
     const int o0 = v0 & (G - 1);
     const uint32_t first = up ? (kAll << o0) & kAll : kAll >> (G - 1 - o0);
-    for (int it = 0; it * 32 <= glast + 1; ++it) {
-        const int g = up ? g0 + 32 * it + lane : g0 - 32 * it - lane;
-        uint32_t mk = 0;
-        if ((unsigned)g <= (unsigned)glast) {
-            const uint4 q = om128[g];
-            mk = wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb));
-            if (it == 0 && lane == 0) mk &= first;
-        }
-        const int cnt = __popc(mk);
-        int incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const uint32_t hit = __ballot_sync(kFull, incl >= need);
-        if (hit) {
+    auto test = [&](int g) -> uint32_t {
+        if ((unsigned)g > (unsigned)glast) return 0u;
+        const uint4 q = om128[g];
+        return wt(q.x) | (wt(q.y) << kb) | (wt(q.z) << (2 * kb)) | (wt(q.w) << (3 * kb));
+    };
+    for (int it = 0; it * 64 <= glast + 1; ++it) {
+        // this lane's two groups, in walking order
+        const int ga = up ? g0 + 64 * it + 2 * lane : g0 - 64 * it - 2 * lane;
+        const int gb = up ? ga + 1 : ga - 1;
+        uint32_t ma = test(ga);
+        const uint32_t mb = test(gb);
+        if (it == 0 && lane == 0) ma &= first;
+        const int cnt = __popc(ma) + __popc(mb);
+        const int total = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+        if (total >= need) {
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t hit = __ballot_sync(kFull, incl >= need);
             const int j = __ffs(hit) - 1;
             int m = 0;
             if (lane == j) {
-                int k = need - (incl - cnt);  // the k-th member of this group, counted along the walk
-                uint32_t mask = mk;
+                int k = need - (incl - cnt);  // the k-th member of this lane's groups, along the walk
+                const int ca = __popc(ma);
+                const int g = k <= ca ? ga : gb;
+                uint32_t mask = k <= ca ? ma : mb;
+                if (k > ca) k -= ca;
                 if (up) {
                     for (; k > 1; --k) mask &= mask - 1;
                     m = G * g + __ffs(mask) - 1;
@@ -310,10 +328,44 @@ __device__ __forceinline__ int wide_select(const typename Loc<W>::E* __restrict_
             }
             return __shfl_sync(kFull, m, j);
         }
-        need -= __shfl_sync(kFull, incl, 31);
-        if (up ? g0 + 32 * (it + 1) > glast : g0 - 32 * (it + 1) < 0) break;
+        need -= total;
+        if (up ? g0 + 64 * (it + 1) > glast : g0 - 64 * (it + 1) < 0) break;
     }
     return -1;
+}
+
+// Members of a window below rank `p` (every lane gets the warp's total). Lane l takes kernel rows
+// l, l + 32, ... and reads each row segment of the ordinal image in aligned 8-rank chunks (one
+// 128-bit load each), comparing the ranks two per 32-bit word; only a row's first and last chunks
+// need a mask. `ctr` is the window centre's ordinal-image position shifted by the kernel's first
+// row (ymin) rows, as in window_walk; the image is 16-byte aligned.
+__device__ __forceinline__ int window_rows_below(const int* spans, int nrows, const uint16_t* ctr, int SP, int p) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t up = (uint32_t)p;
+    int c = 0;
+    for (int i = lane; i < nrows; i += 32) {
+        const int sp = spans[i];
+        const uint16_t* lo = ctr + i * SP + span_lo(sp);
+        const uint16_t* hi = ctr + i * SP + span_hi(sp);
+        const uint4* q = reinterpret_cast<const uint4*>((uintptr_t)lo & ~(uintptr_t)15);
+        const uint4* qe = reinterpret_cast<const uint4*>((uintptr_t)hi & ~(uintptr_t)15);
+        for (; q <= qe; ++q) {
+            const uint4 v = *q;
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            const uint16_t* e0 = reinterpret_cast<const uint16_t*>(q);
+            if (e0 >= lo && e0 + 7 <= hi) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) c += (int)((w[j] & 0xffffu) < up) + (int)((w[j] >> 16) < up);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t r = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                    c += (int)(e0 + j >= lo && e0 + j <= hi && r < up);
+                }
+            }
+        }
+    }
+    return (int)__reduce_add_sync(kFull, (unsigned)c);
 }
 
 // Per-thread exact selection (vertical sweep): every lane refines its own window. It scans the
@@ -958,117 +1010,73 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             G.sync();
         }
         const int nseeds = P.RB * P.G;
-        static_assert(kHidden + kNeigh + 2 * kHidden <= kSeedBins, "MLP activations fit a seed histogram per seed");
+        static_assert(kHidden <= kSeedBins, "the quantiles' layer-1 pre-activations fit one seed histogram");
         if (learned) {
-            // Learned bracket (extension): the bracket MLP runs block-wide over a chunk of seeds
-            // (thread per (seed, hidden unit), activations in the seed-histogram buffers), then one
-            // warp per seed counts its window at the bracket ends and at the predicted median, and
-            // walks Omega 256 entries per step from the prediction (or, on a miss, from the
-            // bracket end the target lies beyond). It replaces the plain seeds' histogram, whose
-            // one shared-memory atomic per window pixel is what makes them expensive.
+            // Learned bracket (extension): the layer-1 contribution of the tile's quantiles is
+            // computed once, block-wide; then each warp takes one seed at a time and, with no
+            // further block barrier, evaluates the bracket MLP for it (lanes hold hidden units
+            // lane and lane + 32, activations move by shuffles), counts the window's ranks below
+            // the predicted median, and walks Omega 512 entries a step from there to the exact
+            // median. It replaces the plain seeds' histogram or long walk.
             const uint16_t* wts =
                 P.off_model >= 0 ? reinterpret_cast<const uint16_t*>(smem_base + P.off_model) : P.model;
-            const int chunk_max = min(nwarps, nseeds);
-            // activations: 64 + chunk * (9 + 64 + 64) floats, within the chunk * 1 KiB of histograms
             float* hbase = reinterpret_cast<float*>(shist);  // layer-1 pre-activation of the quantiles
-            float* xs = hbase + kHidden;                      // [chunk][kNeigh]
-            float* h1 = xs + chunk_max * kNeigh;              // [chunk][kHidden]
-            float* h2 = h1 + chunk_max * kHidden;             // [chunk][kHidden]
             for (int j = tid; j < kHidden; j += nthreads) {
                 float h = bf16_to_f32(wts[kOffB1 + j]);
                 for (int i = 0; i < kQuantiles; ++i) h = fmaf(quant[i], bf16_to_f32(wts[kOffW1 + i * kHidden + j]), h);
                 hbase[j] = h;
             }
-            for (int c0 = 0; c0 < nseeds; c0 += chunk_max) {
-                const int chunk = min(chunk_max, nseeds - c0);
-                if (warp < chunk) {
-                    const int sd = c0 + warp;
-                    const int band = sd / P.G, g = sd % P.G;
-                    const int cu = g * GW + GW / 2 - xmin, cv = band * BH + BH / 2 - ymin;
-                    float fa, fb;
-                    seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
-                    if (lane < kNeigh) xs[warp * kNeigh + lane] = fb;
+            G.sync();
+            for (int sd = warp; sd < nseeds; sd += nwarps) {
+                const int band = sd / P.G, g = sd % P.G;
+                const int s = g * GW + GW / 2, t = band * BH + BH / 2;
+                const int cu = s - xmin, cv = t - ymin;
+                float fa, fb;
+                seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+                float a0 = hbase[lane], a1 = hbase[lane + 32];
+#pragma unroll
+                for (int i = 0; i < kNeigh; ++i) {
+                    const float x = __shfl_sync(kFull, fb, i);
+                    a0 = fmaf(x, bf16_to_f32(wts[kOffW1 + (kQuantiles + i) * kHidden + lane]), a0);
+                    a1 = fmaf(x, bf16_to_f32(wts[kOffW1 + (kQuantiles + i) * kHidden + lane + 32]), a1);
                 }
-                G.sync();
-                for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
-                    const int sl = idx / kHidden, j = idx % kHidden;
-                    float h = hbase[j];
-    #pragma unroll
-                    for (int i = 0; i < kNeigh; ++i)
-                        h = fmaf(xs[sl * kNeigh + i], bf16_to_f32(wts[kOffW1 + (kQuantiles + i) * kHidden + j]), h);
-                    h1[idx] = fmaxf(h, 0.f);
+                a0 = fmaxf(a0, 0.f);
+                a1 = fmaxf(a1, 0.f);
+                float b0 = bf16_to_f32(wts[kOffB2 + lane]), b1 = bf16_to_f32(wts[kOffB2 + lane + 32]);
+#pragma unroll 8
+                for (int k = 0; k < kHidden; ++k) {
+                    const float x = __shfl_sync(kFull, k < 32 ? a0 : a1, k & 31);
+                    b0 = fmaf(x, bf16_to_f32(wts[kOffW2 + k * kHidden + lane]), b0);
+                    b1 = fmaf(x, bf16_to_f32(wts[kOffW2 + k * kHidden + lane + 32]), b1);
                 }
-                G.sync();
-                for (int idx = tid; idx < chunk * kHidden; idx += nthreads) {
-                    const int sl = idx / kHidden, j = idx % kHidden;
-                    float h = bf16_to_f32(wts[kOffB2 + j]);
-    #pragma unroll 8
-                    for (int k = 0; k < kHidden; ++k) h = fmaf(h1[sl * kHidden + k], bf16_to_f32(wts[kOffW2 + k * kHidden + j]), h);
-                    h2[idx] = fmaxf(h, 0.f);
+                b0 = fmaxf(b0, 0.f);
+                b1 = fmaxf(b1, 0.f);
+                float o0 = bf16_to_f32(wts[kOffW3 + lane * 2]) * b0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2]) * b1;
+                float o1 = bf16_to_f32(wts[kOffW3 + lane * 2 + 1]) * b0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2 + 1]) * b1;
+                for (int o = 16; o > 0; o >>= 1) {
+                    o0 += __shfl_xor_sync(kFull, o0, o);
+                    o1 += __shfl_xor_sync(kFull, o1, o);
                 }
-                G.sync();
-                int lo = 0, hi = 0, pmid = 0;
-                if (warp < chunk) {  // output layer: lanes hold hidden units lane and lane + 32
-                    const float x0 = h2[warp * kHidden + lane], x1 = h2[warp * kHidden + lane + 32];
-                    float o0 = bf16_to_f32(wts[kOffW3 + lane * 2]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2]) * x1;
-                    float o1 = bf16_to_f32(wts[kOffW3 + lane * 2 + 1]) * x0 + bf16_to_f32(wts[kOffW3 + (lane + 32) * 2 + 1]) * x1;
-                    for (int o = 16; o > 0; o >>= 1) {
-                        o0 += __shfl_xor_sync(kFull, o0, o);
-                        o1 += __shfl_xor_sync(kFull, o1, o);
-                    }
-                    o0 += bf16_to_f32(wts[kOffB3]);
-                    o1 += bf16_to_f32(wts[kOffB3 + 1]);
-                    const float sig = __expf(fminf(fmaxf(o1, -8.f), 2.f)) * P.bracket_z;
-                    const float span = (float)(hif - lof);
-                    lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
-                    hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
-                    pmid = clampi(__float2int_rn(lof + o0 * span), lo, hi);
+                o0 += bf16_to_f32(wts[kOffB3]);
+                o1 += bf16_to_f32(wts[kOffB3 + 1]);
+                const float sig = __expf(fminf(fmaxf(o1, -8.f), 2.f)) * P.bracket_z;
+                const float span = (float)(hif - lof);
+                const int lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
+                const int hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
+                const int pivot = clampi(__float2int_rn(lof + o0 * span), lo, hi);
+                // The count at the predicted median is exact, so the walk from it finds the exact
+                // median wherever it lies: on a miss it simply walks past the bracket, over the
+                // full range if need be. The bracket ends only classify the outcome.
+                const int below = window_rows_below(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, pivot);
+                const int m = wide_select<SHAPE, W>(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+                if (m < 0) set_status(FIM_ERR_INTERNAL);
+                if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+                if (counting && lane == 0) {
+                    const int kind = m < lo ? 2 : (m > hi ? 3 : 1);
+                    atomicAdd(P.stats + 0, 1ull);
+                    atomicAdd(P.stats + kind, 1ull);
+                    atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
                 }
-                G.sync();  // the activation buffers are reused by the next chunk
-                if (warp < chunk) {
-                    const int sd = c0 + warp;
-                    const int band = sd / P.G, g = sd % P.G;
-                    const int s = g * GW + GW / 2, t = band * BH + BH / 2;
-                    const int cu = s - xmin, cv = t - ymin;
-                    // One pass counts the window's ranks below the bracket's low end, below the
-                    // predicted median and up to the high end: compares and adds only, no
-                    // histogram and no atomics. The walk then starts at the prediction (a hit) or
-                    // at the bracket end the target lies beyond (a miss), so its length is the
-                    // prediction's error, whatever it is: the output stays exact.
-                    const int mid = clampi(pmid, lo, hi);
-                    int clo = 0, cmid = 0, chi = 0;
-                    window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, [&](int r) {
-                        clo += r < lo;
-                        cmid += r < mid;
-                        chi += r <= hi;
-                    });
-                    clo = __reduce_add_sync(kFull, clo);
-                    cmid = __reduce_add_sync(kFull, cmid);
-                    chi = __reduce_add_sync(kFull, chi);
-                    int pivot, below, kind;
-                    if (target < clo) {         // below the bracket: walk down from lo
-                        pivot = lo;
-                        below = clo;
-                        kind = 2;
-                    } else if (target >= chi) { // above the bracket: walk up from hi + 1
-                        pivot = hi + 1;
-                        below = chi;
-                        kind = 3;
-                    } else {                    // inside: walk from the predicted median
-                        pivot = mid;
-                        below = cmid;
-                        kind = 1;
-                    }
-                    const int m = wide_select<SHAPE, W>(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
-                    if (m < 0) set_status(FIM_ERR_INTERNAL);
-                    if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
-                    if (counting && lane == 0) {
-                        atomicAdd(P.stats + 0, 1ull);
-                        atomicAdd(P.stats + kind, 1ull);
-                        atomicAdd(P.stats + 4, (unsigned long long)abs(max(m, 0) - pivot));
-                    }
-                }
-                G.sync();  // the next chunk reuses the activation buffers
             }
         } else {
             for (int sd = warp; sd < nseeds; sd += nwarps) {
@@ -1077,17 +1085,34 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
                 float fa = 0.f, fb = 0.f;
                 if (sampling) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
-                // one histogram per concurrently solved seed
-                uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
-                for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
-                __syncwarp();
-                window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
-                            [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
-                __syncwarp();
-                int below = 0;
                 const int ts = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
-                const int pivot = hist_pick(hw, 0, ts, &below) << hist_shift;
-                const int m = ballot_select(om, N, pivot, below, ts, cu - cx0, cv - cy0, member);
+                int pivot = 0, below = 0, m;
+                if (P.seed_mode == kSeedHistogram) {
+                    // a coarse histogram of the window's ranks (one per concurrently solved seed),
+                    // scanned to the bin of the target, then a ballot scan of Omega from that bin
+                    uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
+                    for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
+                    __syncwarp();
+                    window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
+                                [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
+                    __syncwarp();
+                    pivot = hist_pick(hw, 0, ts, &below) << hist_shift;
+                    m = ballot_select(om, N, pivot, below, ts, cu - cx0, cv - cy0, member);
+                } else {
+                    if (P.seed_mode == kSeedWalk) {
+                        // walk Omega from whichever end is known exactly: nothing lies below
+                        // rank 0, and all n members lie below rank N
+                        if (2 * ts >= P.n) {
+                            pivot = N;
+                            below = P.n;
+                        }
+                    } else {
+                        // count the window below the middle of the tile's feasible ranks, walk from there
+                        pivot = (lof + hif) >> 1;
+                        below = window_rows_below(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, pivot);
+                    }
+                    m = wide_select<SHAPE, W>(om, N, pivot, below, ts, cu - cx0, cv - cy0, member);
+                }
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
                 if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
                 if (sampling) {  // training row: features and the exact median's place in [lof, hif]

@@ -1,7 +1,8 @@
 // Autotuner: picks the tile configuration (tile width and height, bands, seeds per seed row)
-// for a (device, dtype, kernel geometry) by timing every valid candidate on the caller's data
-// with CUDA events. Results live in a process-wide cache that choose_tile() consults first and
-// that can be persisted to a text file named by the FIM_TUNE_CACHE environment variable.
+// for a (device, dtype, kernel geometry, image-size class) by timing every valid candidate on the
+// caller's data with CUDA events. Results live in a process-wide cache that choose_tile()
+// consults first and that can be persisted to a text file named by the FIM_TUNE_CACHE
+// environment variable.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -18,7 +19,8 @@
 namespace fim {
 namespace {
 
-using Key = std::tuple<std::string, int, uint64_t, int>;  // device name, dtype, kernel hash, CTA size (0: any)
+// device name, dtype, kernel hash, CTA size (0: any), image-size class
+using Key = std::tuple<std::string, int, uint64_t, int, int>;
 
 std::mutex g_tune_mu;
 std::map<Key, TileShape>& tune_map() {
@@ -69,10 +71,10 @@ void load_locked() {
     FILE* f = fopen(path, "r");
     if (!f) return;
     char name[256];
-    int dtype, cta, tx, ty, rb, g;
+    int dtype, cta, sc, tx, ty, rb, g;
     unsigned long long hash;
-    while (fscanf(f, "%255s %d %llx %d %d %d %d %d", name, &dtype, &hash, &cta, &tx, &ty, &rb, &g) == 8)
-        tune_map()[Key(std::string(name), dtype, (uint64_t)hash, cta)] = TileShape{tx, ty, rb, g};
+    while (fscanf(f, "%255s %d %llx %d %d %d %d %d %d", name, &dtype, &hash, &cta, &sc, &tx, &ty, &rb, &g) == 9)
+        tune_map()[Key(std::string(name), dtype, (uint64_t)hash, cta, sc)] = TileShape{tx, ty, rb, g};
     fclose(f);
 }
 
@@ -83,28 +85,28 @@ void save_locked() {
     FILE* f = fopen(tmp.c_str(), "w");
     if (!f) return;
     for (const auto& kv : tune_map())
-        fprintf(f, "%s %d %llx %d %d %d %d %d\n", std::get<0>(kv.first).c_str(), std::get<1>(kv.first),
-                (unsigned long long)std::get<2>(kv.first), std::get<3>(kv.first), kv.second.Tx, kv.second.Ty,
-                kv.second.RB, kv.second.G);
+        fprintf(f, "%s %d %llx %d %d %d %d %d %d\n", std::get<0>(kv.first).c_str(), std::get<1>(kv.first),
+                (unsigned long long)std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first),
+                kv.second.Tx, kv.second.Ty, kv.second.RB, kv.second.G);
     fclose(f);
     rename(tmp.c_str(), path);
 }
 
 }  // namespace
 
-bool tuned_lookup(const fim_kernel* k, int dtype, TileShape* ts, int cta_threads) {
+bool tuned_lookup(const fim_kernel* k, int dtype, TileShape* ts, int size_cls, int cta_threads) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     load_locked();
-    auto it = tune_map().find(Key(device_name(), dtype, kernel_hash(k), cta_threads));
+    auto it = tune_map().find(Key(device_name(), dtype, kernel_hash(k), cta_threads, size_cls));
     if (it == tune_map().end()) return false;
     *ts = it->second;
     return true;
 }
 
-void tuned_store(const fim_kernel* k, int dtype, const TileShape& ts, int cta_threads) {
+void tuned_store(const fim_kernel* k, int dtype, const TileShape& ts, int size_cls, int cta_threads) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     load_locked();
-    tune_map()[Key(device_name(), dtype, kernel_hash(k), cta_threads)] = ts;
+    tune_map()[Key(device_name(), dtype, kernel_hash(k), cta_threads, size_cls)] = ts;
     save_locked();
 }
 
@@ -183,7 +185,7 @@ extern "C" fim_status fim_autotune(const void* in, void* out, int w, int h, size
     delete p;
     if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;
     if (result == FIM_OK) {
-        tuned_store(k, dtype, best, cta_threads);
+        tuned_store(k, dtype, best, size_class(w, h), cta_threads);
         if (tile_w) *tile_w = best.Tx;
         if (tile_h) *tile_h = best.Ty;
     }
