@@ -541,6 +541,60 @@ def multi_percentile_section(fim, torch, img, reps: int = 5):
 
 
 # ---------------------------------------------------------------------------------------------
+# several radii from one ordinal transform vs one launch per radius
+# ---------------------------------------------------------------------------------------------
+
+def radii_section(fim, torch, src_u16, reps: int = 3):
+    """fim_median_radii (one sort per tile, for the largest disk) against one fim_median launch
+    per radius, on the 4096x4096 u16 image at Sec. 6.2's radii 8/16/32 and 32/48/64, and on a
+    4096x4096 float field at r = 64/100, where the sort dominates. Output Mpix/s counts every
+    output image; the outputs are compared bytewise."""
+    import datagen
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    f32 = datagen.torch_field_f32(datagen.seed_for(3, 0), 4096, 4096)
+    cases = [("u16", src_u16, fim.FIM_U16, (8, 16, 32)), ("u16", src_u16, fim.FIM_U16, (32, 48, 64)),
+             ("f32", f32, fim.FIM_F32, (64, 100))]
+    res = {}
+    same = True
+    for name, img, code, radii in cases:
+        h, w = img.shape
+        pitch = img.stride(0) * img.element_size()
+        ks = [fim.fim_create_kernel_circle(r) for r in radii]
+        outs_m = [torch.empty_like(img) for _ in radii]
+        outs_s = [torch.empty_like(img) for _ in radii]
+
+        def multi():
+            fim.fim_median_radii(img.data_ptr(), [o.data_ptr() for o in outs_m], ks, w, h, pitch, code, sh)
+
+        def single():
+            for k, o in zip(ks, outs_s):
+                fim.fim_median(img.data_ptr(), o.data_ptr(), w, h, pitch, code, k, sh)
+
+        multi()
+        single()
+        times = {}
+        for nm, fn in (("multi", multi), ("single", single)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times[nm] = a.elapsed_time(b) / reps
+        iv = (lambda t: t.view(torch.int16)) if img.dtype == torch.uint16 else (lambda t: t.view(torch.int32))
+        same = same and all(torch.equal(iv(x), iv(y)) for x, y in zip(outs_m, outs_s))
+        mpix = len(radii) * w * h / 1e6
+        res[f"{name}_r" + "_".join(map(str, radii))] = {
+            "Mpix_s_one_launch": mpix / (times["multi"] * 1e-3),
+            "Mpix_s_one_launch_per_radius": mpix / (times["single"] * 1e-3),
+            "speedup": times["single"] / times["multi"]}
+    del f32
+    return {"workload": "4096x4096 u16 photo-like (r 8/16/32 and 32/48/64) and f32 field (r 64/100)",
+            "cases": res, "bit_exact_vs_single": bool(same), "status": fim.fim_sync_status(sh)}
+
+
+# ---------------------------------------------------------------------------------------------
 # learned seed bracket vs plain seeds (6000x4000x3 u16, r = 48)
 # ---------------------------------------------------------------------------------------------
 
@@ -851,6 +905,9 @@ def run_native(args):
         line["batched"] = batched_section(fim, torch)
     if world == 1 and not args.no_multi:
         line["percentiles"] = multi_percentile_section(fim, torch, src)
+        line["radii"] = radii_section(fim, torch, src)
+        if not line["radii"]["bit_exact_vs_single"] or line["radii"]["status"]:
+            failed.append("radii")
     if world == 1 and not args.no_learned:
         line["learned"] = learned_section(fim, torch, args.train_images)
     if failed:

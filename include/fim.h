@@ -144,6 +144,23 @@ fim_status fim_percentiles(const void* in, void* const* outs, const double* perc
                            size_t pitch_bytes, fim_dtype dtype, const fim_kernel* k, fim_border border, void* stream);
 
 /*
+ * Median filters of one image with several disk kernels, in one launch: each tile's ordinal
+ * transform and ordinal image are built once, for the footprint of the largest disk, and serve
+ * every disk (its seeds, slides and scans run with its own tables and membership test over the
+ * same omnigram). Sec. 6.2 proposes filtering several radii (its example: 8, 16, 32) from one
+ * transform; the paper's own implementation filters one radius at a time.
+ * kernels: `count` (1..8) handles made by fim_create_kernel_circle / _disk_limit (any other
+ * shape: FIM_ERR_INVALID_ARG), host array; outs: `count` device pointers, host array, output q
+ * receiving the median with kernels[q], each with the input's pitch. The tile shape is the one
+ * the largest disk takes. Same argument checks and errors as fim_median for every (out, kernel)
+ * pair, plus FIM_ERR_INVALID_ARG for count outside 1..8; outputs that overlap one another race.
+ * Asynchronous on `stream`; the per-kernel tables go to stream-ordered device memory
+ * (cudaMallocAsync) for the launch's duration.
+ */
+fim_status fim_median_radii(const void* in, void* const* outs, const fim_kernel* const* kernels, int count, int w,
+                            int h, size_t pitch_bytes, fim_dtype dtype, fim_border border, void* stream);
+
+/*
  * Spatially varying percentile (Fig. 14): every output pixel takes its own percentile from a
  * device float32 map. percentiles: w x h values, rows pct_pitch_bytes apart (>= 4 * w, a
  * multiple of 4); read only, owned by the caller, must not overlap the output and must stay

@@ -43,6 +43,8 @@ SIGNATURES = {
                                    _c.c_int, _P]),
     "fim_percentile_map": (_c.c_int, [_P, _P, _P, _c.c_size_t, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P,
                                       _c.c_int, _P]),
+    "fim_median_radii": (_c.c_int, [_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_int,
+                                    _P]),
     "fim_median_host": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
     "fim_median_noalloc": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _P, _c.c_int, _P]),
     "fim_sync_status": (_c.c_int, [_P]),
@@ -208,6 +210,16 @@ def fim_percentiles(in_ptr: int, out_ptrs, percentiles, w: int, h: int, pitch_by
     pcts = (_c.c_double * max(len(percentiles), 1))(*[float(x) for x in percentiles])
     _check(lib().fim_percentiles(in_ptr, outs, pcts, count, w, h, pitch_bytes, dtype, kernel.handle, border,
                                  stream or None), "fim_percentiles")
+
+
+def fim_median_radii(in_ptr: int, out_ptrs, kernels, w: int, h: int, pitch_bytes: int, dtype: int,
+                     stream: int = 0, border: int = FIM_BORDER_CLAMP) -> None:
+    """Median filters with several disk kernels from one ordinal transform per tile."""
+    count = len(out_ptrs)
+    outs = (_c.c_void_p * max(count, 1))(*[_c.c_void_p(p) for p in out_ptrs])
+    ks = (_c.c_void_p * max(len(kernels), 1))(*[k.handle for k in kernels])
+    _check(lib().fim_median_radii(in_ptr, outs, ks, count, w, h, pitch_bytes, dtype, border, stream or None),
+           "fim_median_radii")
 
 
 def fim_percentile_map(in_ptr: int, out_ptr: int, pct_ptr: int, pct_pitch_bytes: int, w: int, h: int,
@@ -455,6 +467,20 @@ def percentiles(img, kernel: Kernel, pcts, stream=None):
     h, w = img.shape
     fim_percentiles(img.data_ptr(), [o.data_ptr() for o in outs], list(pcts), w, h, pitch, code, kernel,
                     _stream_handle(stream))
+    return outs
+
+
+def median_radii(img, kernels, stream=None):
+    """Returns one median-filtered image per disk kernel in `kernels` (at most 8), all from one
+    launch."""
+    import torch
+    assert img.is_cuda and img.dim() == 2 and img.stride(1) == 1
+    code = _torch_dtype_code(img)
+    outs = [torch.empty_strided(img.shape, img.stride(), dtype=img.dtype, device=img.device) for _ in kernels]
+    pitch = img.stride(0) * img.element_size()
+    h, w = img.shape
+    fim_median_radii(img.data_ptr(), [o.data_ptr() for o in outs], list(kernels), w, h, pitch, code,
+                     _stream_handle(stream))
     return outs
 
 

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "fim_internal.h"
 
@@ -311,6 +312,7 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
     take_tab(&p->off_frow, (size_t)p->SH * 4);
     p->off_model = -1;
     if (stage_model) take_tab(&p->off_model, (size_t)kMlpParams * 2);
+    if (p->xtab_words > 0) take_tab(&p->off_xtab, (size_t)p->xtab_words * 4);
     p->tab_bytes = (int)tab;  // everything from here on belongs to one tile group
     p->off_misc = (int)tab;
     tab += 256;
@@ -731,6 +733,116 @@ fim_status fim_percentiles(const void* in, void* const* outs, const double* perc
         get_phase_clock_buffer(&p->phase_clock, &p->phase_tiles);
         s = launch_tile_kernel(*p, (cudaStream_t)stream);
     }
+    delete p;
+    return s;
+}
+
+fim_status fim_median_radii(const void* in, void* const* outs, const fim_kernel* const* kernels, int count, int w,
+                            int h, size_t pitch_bytes, fim_dtype dtype, fim_border border, void* stream) {
+    if (!outs || !kernels || count < 1 || count > kMaxRanks) return FIM_ERR_INVALID_ARG;
+    int big = 0;  // the largest disk: its footprint holds every other disk's windows
+    for (int i = 0; i < count; ++i) {
+        fim_status s = check_image_args(in, outs[i], w, h, pitch_bytes, dtype, kernels[i], border);
+        if (s != FIM_OK) return s;
+        if (kernels[i]->shape != kShapeDisk) return FIM_ERR_INVALID_ARG;
+        if (kernels[i]->r2 > kernels[big]->r2) big = i;
+    }
+    static thread_local int smem_limit = -1;
+    if (smem_limit < 0) smem_limit = device_smem_limit();
+    if (smem_limit <= 0) return FIM_ERR_CUDA;
+    const fim_kernel* kb = kernels[big];
+    TileShape ts;
+    fim_status s = choose_tile(kb, dtype, smem_limit, &ts, w, h);
+    if (s != FIM_OK) return s;
+    Plan* p = new (std::nothrow) Plan;
+    if (!p) return FIM_ERR_OOM;
+    s = make_plan(kb, dtype, (kb->n - 1) / 2, w, h, ts, smem_limit, p);
+    // Targets run largest disk first, so that each footprint holds the next one and the tile can
+    // narrow its omnigram from disk to disk. Every disk's tables (per-column vertical-slide
+    // offsets, per-row horizontal offsets and spans) are relative to the window centre in the
+    // largest disk's footprint box; its footprint rows are in that box's coordinates.
+    int order[kMaxRanks];
+    for (int q = 0; q < count; ++q) order[q] = q;
+    std::stable_sort(order, order + count, [&](int a, int b) { return kernels[a]->r2 > kernels[b]->r2; });
+    std::vector<int> xt;
+    int rel_v[kMaxRanks], rel_h[kMaxRanks], rel_s[kMaxRanks], rel_f[kMaxRanks];
+    if (s == FIM_OK) {
+        const int SP = p->SP, SH = p->SH, Tx = p->Tx, Ty = p->Ty;
+        for (int q = 0; q < count; ++q) {
+            const fim_kernel* k = kernels[order[q]];
+            const int nrows = k->ymax - k->ymin + 1, ncols = k->xmax - k->xmin + 1;
+            rel_v[q] = (int)xt.size();
+            for (int j = 0; j < ncols; ++j) {
+                xt.push_back(k->ctop[j] * SP + k->xmin + j);
+                xt.push_back((k->cbot[j] + 1) * SP + k->xmin + j);
+            }
+            rel_h[q] = (int)xt.size();
+            for (int i = 0; i < nrows; ++i) {
+                xt.push_back((k->ymin + i) * SP + k->rlo[i]);
+                xt.push_back((k->ymin + i) * SP + k->rhi[i] + 1);
+            }
+            rel_s[q] = (int)xt.size();
+            for (int i = 0; i < nrows; ++i) xt.push_back((int)((uint32_t)(k->rlo[i] & 0xffff) | ((uint32_t)k->rhi[i] << 16)));
+            // this disk's footprint (Fig. 10) in the box: row v holds the columns of the tile's
+            // windows whose kernel row i meets box row v
+            rel_f[q] = (int)xt.size();
+            long long nq = 0;
+            for (int v = 0; v < SH; ++v) {
+                const int i0 = std::max(0, v + p->ymin - k->ymin - Ty + 1), i1 = std::min(nrows - 1, v + p->ymin - k->ymin);
+                int lo = 1 << 14, hi = -(1 << 14);
+                for (int i = i0; i <= i1; ++i) {
+                    lo = std::min(lo, k->rlo[i] - p->xmin);
+                    hi = std::max(hi, k->rhi[i] + Tx - 1 - p->xmin);
+                }
+                if (lo > hi) lo = 1, hi = 0;  // no pixel of this row
+                xt.push_back((int)((uint32_t)(lo & 0xffff) | ((uint32_t)hi << 16)));
+                nq += hi - lo + 1;
+            }
+            if (xt.size() & 1) xt.push_back(0);  // the next disk's int2 tables stay 8-byte aligned
+            p->q_r2[q] = (int)k->r2;
+            p->q_n[q] = k->n;
+            p->q_ymin[q] = k->ymin;
+            p->q_nrows[q] = nrows;
+            p->q_ncols[q] = ncols;
+            p->q_N[q] = (int)nq;
+            int hs = 0;
+            while (((nq - 1) >> hs) >= kSeedBins) ++hs;
+            p->q_hshift[q] = hs;
+            p->q_vmix[q] = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1 <= 40 ? 1 : 0;
+            p->ranks[q] = (k->n - 1) / 2;
+            p->outs[q] = outs[order[q]];
+        }
+        p->xtab_words = (int)xt.size();
+        s = layout_plan(p, smem_limit);
+    }
+    int* dx = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s == FIM_OK) {
+        if (cudaMallocAsync(reinterpret_cast<void**>(&dx), xt.size() * 4, st) != cudaSuccess) {
+            cudaGetLastError();
+            s = FIM_ERR_OOM;
+        } else if (cudaMemcpyAsync(dx, xt.data(), xt.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            s = FIM_ERR_CUDA;
+        }
+    }
+    if (s == FIM_OK) {
+        for (int q = 0; q < count; ++q) {
+            p->q_vtab[q] = p->off_xtab + 4 * rel_v[q];
+            p->q_htab[q] = p->off_xtab + 4 * rel_h[q];
+            p->q_spans[q] = p->off_xtab + 4 * rel_s[q];
+            p->q_frow[q] = p->off_xtab + 4 * rel_f[q];
+        }
+        p->multi = 1;
+        p->xtab = dx;
+        p->in = in;
+        p->out = p->outs[0];
+        p->rank = p->ranks[0];
+        p->pitch = (long long)pitch_bytes;
+        p->nranks = count;
+        get_phase_clock_buffer(&p->phase_clock, &p->phase_tiles);
+        s = launch_tile_kernel(*p, st);
+    }
+    if (dx && cudaFreeAsync(dx, st) != cudaSuccess && s == FIM_OK) s = FIM_ERR_CUDA;
     delete p;
     return s;
 }

@@ -92,6 +92,17 @@ struct Plan {
     int nranks;             // extras kernels: target ranks served by one ordinal transform (1..kMaxRanks)
     int ranks[kMaxRanks];   //   their ranks; entry 0 is taken from `rank`
     void* outs[kMaxRanks];  //   and their outputs (same pitch as the input); entry 0 is taken from `out`
+    // several disks from one transform (fim_median_radii): every target has a kernel of its own,
+    // nested in the plan's kernel (which sets the footprint); its tables sit in shared memory
+    int multi;                          // 1: the q_ arrays below give each target's kernel
+    int q_vtab[kMaxRanks], q_htab[kMaxRanks], q_spans[kMaxRanks];  // shared-memory byte offsets
+    int q_r2[kMaxRanks], q_n[kMaxRanks], q_ymin[kMaxRanks], q_nrows[kMaxRanks], q_ncols[kMaxRanks];
+    int q_frow[kMaxRanks];              // shared-memory byte offset of each disk's footprint rows
+    int q_N[kMaxRanks], q_hshift[kMaxRanks];  // its footprint size and seed-histogram shift
+    int q_vmix[kMaxRanks];              // its vertical-sweep lane mixing (as `vmix` for its own plan)
+    const int* xtab;                    // device: those tables, copied to shared memory at off_xtab
+    int xtab_words;                     // their length in 32-bit words
+    int off_xtab;
     // footprint
     int N;                  // pixels in the rounded-rectangle footprint
     int cx0, cy0;           // omnigram coordinates are stored as (u - cx0, v - cy0), int8 each

@@ -6,7 +6,7 @@ namespace fim {
 
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream) {
     if (p.rank_map != nullptr) return launch_tile_kernel_map(p, stream);
-    if (p.model != nullptr || p.samples != nullptr || p.stats != nullptr || p.nranks > 1)
+    if (p.model != nullptr || p.samples != nullptr || p.stats != nullptr || p.nranks > 1 || p.multi)
         return launch_tile_kernel_extras(p, stream);
     return p.scan_groups == 4 ? launch_tile_kernel_k4(p, stream) : launch_tile_kernel_ks<8>(p, stream);
 }

@@ -892,6 +892,72 @@ __device__ __forceinline__ T* place(unsigned char* smem, unsigned char* gslice, 
     return reinterpret_cast<T*>(loc >= 0 ? smem + loc : gslice + (-(long long)loc - 1));
 }
 
+// Several radii from one transform: keeps, in order, the omnigram entries that lie in a smaller
+// disk's footprint (`qfrow`: per box row, its columns lo | hi << 16; rows outside hold an empty
+// span), and gives those pixels their new ranks in the ordinal image. The order of the kept
+// entries is the sorted order restricted to the smaller footprint, i.e. that footprint's own
+// ordinal transform, obtained in one pass with no sort. Each thread takes 4 consecutive entries
+// of a 4 * group-size chunk; a block scan of the per-thread counts gives the new places. Every
+// write goes to an index no larger than the entry's own, and all reads of a chunk precede its
+// first barrier, so the compaction can run in place. Returns the number kept.
+template <int W>
+__device__ int compact_omnigram(typename Loc<W>::E* om, int N, const int* qfrow, uint16_t* ord, int SP, int cx0,
+                                int cy0, uint32_t* wsum, const Grp& G, int nthreads, int nwarps) {
+    using E = typename Loc<W>::E;
+    const int tid = G.tid, lane = G.lane, warp = G.warp;
+    int base = 0;
+    for (int c0 = 0; c0 < N; c0 += 4 * nthreads) {
+        E e[4];
+        bool keep[4];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = c0 + 4 * tid + k;
+            keep[k] = false;
+            e[k] = 0;
+            if (i < N) {
+                e[k] = om[i];
+                const int u = Loc<W>::x(e[k]) + cx0, v = Loc<W>::y(e[k]) + cy0;
+                const int fr = qfrow[v];
+                keep[k] = u >= span_lo(fr) && u <= span_hi(fr);
+            }
+            cnt += keep[k];
+        }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = (uint32_t)incl;
+        G.sync();
+        if (warp == 0) {
+            const uint32_t x = lane < nwarps ? wsum[lane] : 0u;
+            uint32_t y = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, y, o);
+                if (lane >= o) y += t;
+            }
+            wsum[lane] = y - x;         // exclusive per-warp offsets
+            if (lane == 31) wsum[32] = y;  // the chunk's total
+        }
+        G.sync();
+        int idx = base + (int)wsum[warp] + incl - cnt;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (keep[k]) {
+                om[idx] = e[k];
+                ord[(Loc<W>::y(e[k]) + cy0) * SP + Loc<W>::x(e[k]) + cx0] = (uint16_t)idx;
+                ++idx;
+            }
+        base += (int)wsum[32];
+        G.sync();  // the offsets are read before the next chunk rewrites them
+    }
+    const int pad = ((base + Loc<W>::kGroup - 1) & ~(Loc<W>::kGroup - 1)) - base;
+    if (tid < pad) om[base + tid] = Loc<W>::kSentinel;
+    G.sync();
+    return base;
+}
+
 // KS: omnigram groups per scan step of the vertical sweep, fixed at compile time (4 or 8), or
 // 0 to follow the plan's scan_groups at run time (the batch kernel, which serves every plan:
 // one run-time loop keeps its 18 inlined pipelines small enough to compile quickly).
@@ -983,12 +1049,45 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     // previous window's result, which has exactly that window's target below it, so the count
     // at the pivot after the slide is the previous target plus the change.
     const bool mapped = XT == 2 && P.rank_map != nullptr;
+    int Nq = N;  // omnigram length for this target (several radii: the current disk's footprint)
     for (int q = 0; q < nr; ++q) {
         const int target = q == 0 ? P.rank : P.ranks[q];
+        // the kernel of this target: the plan's own, or (several radii) the q-th disk's tables
+        const int2* qvtab = vtab;
+        const int2* qhtab = htab;
+        const int* qspans = spans;
+        int qn = P.n, qymin = ymin, qnrows = P.nrows, qncols = P.ncols;
+        Member<SHAPE, W> qmember = member;
+        if constexpr (XT == 1) {
+            if (P.multi) {
+                qvtab = reinterpret_cast<const int2*>(smem_base + P.q_vtab[q]);
+                qhtab = reinterpret_cast<const int2*>(smem_base + P.q_htab[q]);
+                qspans = reinterpret_cast<const int*>(smem_base + P.q_spans[q]);
+                qn = P.q_n[q];
+                qymin = P.q_ymin[q];
+                qnrows = P.q_nrows[q];
+                qncols = P.q_ncols[q];
+                if constexpr (SHAPE == kShapeDisk) {
+                    qmember.r2 = P.q_r2[q];
+                } else {
+                    qmember.spans = qspans;
+                    qmember.ymin = qymin;
+                    qmember.nrows = qnrows;
+                }
+                // targets come largest disk first: narrow the omnigram to this disk's footprint
+                if (P.q_N[q] < Nq) {
+                    const int kept = compact_omnigram<W>(om, Nq, reinterpret_cast<const int*>(smem_base + P.q_frow[q]),
+                                                         ord, SP, cx0, cy0, misc, G, nthreads, nwarps);
+                    if (kept != P.q_N[q]) set_status(FIM_ERR_INTERNAL);
+                    Nq = P.q_N[q];
+                }
+            }
+        }
+        const int qhist_shift = XT == 1 && P.multi ? P.q_hshift[q] : hist_shift;
         const int BH = TY / P.RB;      // band height
         const int GW = TX / P.G;       // seed spacing within a seed row
         // feasible median ranks of any window of this tile (Fig. 10): [lof, hif]
-        const int lof = target, hif = N - P.n + target;
+        const int lof = target, hif = Nq - qn + target;
 
         // ---- 3. seeds: coarse histogram of I over the window, then ballot refine ----------------
         // (or, with a learned bracket, two exact counts at predicted ranks, then ballot refine)
@@ -999,7 +1098,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
         float* quant = reinterpret_cast<float*>(misc);  // the sort's scan scratch is free from here on
         if (learned || sampling) {
             if (warp == 0) {  // normalised value quantiles of the footprint: C at N (j + 1/2) / 32
-                const int q = min(N - 1, (int)(((long long)N * (2 * lane + 1)) / (2 * kQuantiles)));
+                const int q = min(Nq - 1, (int)(((long long)Nq * (2 * lane + 1)) / (2 * kQuantiles)));
                 const uint32_t e = om[q];
                 const float v = (float)load_px<DT>(Img(P), gx0 + Loc<W>::x(e) + cx0, gy0 + Loc<W>::y(e) + cy0);
                 const float mid = __shfl_sync(kFull, v, kQuantiles / 2);
@@ -1032,7 +1131,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 const int s = g * GW + GW / 2, t = band * BH + BH / 2;
                 const int cu = s - xmin, cv = t - ymin;
                 float fa, fb;
-                seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+                seed_features(ord, SP, frow, P.SH, Nq, cu, cv, quant, &fa, &fb);
                 float a0 = hbase[lane], a1 = hbase[lane + 32];
 #pragma unroll
                 for (int i = 0; i < kNeigh; ++i) {
@@ -1061,14 +1160,14 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 o1 += bf16_to_f32(wts[kOffB3 + 1]);
                 const float sig = __expf(fminf(fmaxf(o1, -8.f), 2.f)) * P.bracket_z;
                 const float span = (float)(hif - lof);
-                const int lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, N - 1);
-                const int hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, N - 1);
+                const int lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, Nq - 1);
+                const int hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, Nq - 1);
                 const int pivot = clampi(__float2int_rn(lof + o0 * span), lo, hi);
                 // The count at the predicted median is exact, so the walk from it finds the exact
                 // median wherever it lies: on a miss it simply walks past the bracket, over the
                 // full range if need be. The bracket ends only classify the outcome.
-                const int below = window_rows_below(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, pivot);
-                const int m = wide_select<SHAPE, W>(om, N, pivot, below, target, cu - cx0, cv - cy0, member);
+                const int below = window_rows_below(qspans, qnrows, ord + (cv + qymin) * SP + cu, SP, pivot);
+                const int m = wide_select<SHAPE, W>(om, Nq, pivot, below, target, cu - cx0, cv - cy0, qmember);
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
                 if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
                 if (counting && lane == 0) {
@@ -1084,7 +1183,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 const int s = g * GW + GW / 2, t = band * BH + BH / 2;  // tile-local output pixel
                 const int cu = s - xmin, cv = t - ymin;                 // window centre in the box
                 float fa = 0.f, fb = 0.f;
-                if (sampling) seed_features(ord, SP, frow, P.SH, N, cu, cv, quant, &fa, &fb);
+                if (sampling) seed_features(ord, SP, frow, P.SH, Nq, cu, cv, quant, &fa, &fb);
                 const int ts = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
                 int pivot = 0, below = 0, m;
                 if (P.seed_mode == kSeedHistogram) {
@@ -1093,25 +1192,25 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                     uint32_t* hw = shist + (nwarps >= nseeds ? sd : warp) * kSeedBins;
                     for (int j = lane; j < kSeedBins; j += 32) hw[j] = 0;
                     __syncwarp();
-                    window_walk(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP,
-                                [&](int r) { atomicAdd(&hw[r >> hist_shift], 1u); });
+                    window_walk(qspans, qnrows, ord + (cv + qymin) * SP + cu, SP,
+                                [&](int r) { atomicAdd(&hw[r >> qhist_shift], 1u); });
                     __syncwarp();
-                    pivot = hist_pick(hw, 0, ts, &below) << hist_shift;
-                    m = ballot_select(om, N, pivot, below, ts, cu - cx0, cv - cy0, member);
+                    pivot = hist_pick(hw, 0, ts, &below) << qhist_shift;
+                    m = ballot_select(om, Nq, pivot, below, ts, cu - cx0, cv - cy0, qmember);
                 } else {
                     if (P.seed_mode == kSeedWalk) {
                         // walk Omega from whichever end is known exactly: nothing lies below
                         // rank 0, and all n members lie below rank N
-                        if (2 * ts >= P.n) {
-                            pivot = N;
-                            below = P.n;
+                        if (2 * ts >= qn) {
+                            pivot = Nq;
+                            below = qn;
                         }
                     } else {
                         // count the window below the middle of the tile's feasible ranks, walk from there
                         pivot = (lof + hif) >> 1;
-                        below = window_rows_below(spans, P.nrows, ord + (cv + ymin) * SP + cu, SP, pivot);
+                        below = window_rows_below(qspans, qnrows, ord + (cv + qymin) * SP + cu, SP, pivot);
                     }
-                    m = wide_select<SHAPE, W>(om, N, pivot, below, ts, cu - cx0, cv - cy0, member);
+                    m = wide_select<SHAPE, W>(om, Nq, pivot, below, ts, cu - cx0, cv - cy0, qmember);
                 }
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
                 if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
@@ -1152,8 +1251,8 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             for (int q = 0; q < kRowsPerLane; ++q) {
                 const int i = lane + 32 * q;
                 eo[q] = lo[q] = 0;  // rows beyond the kernel compare the centre with itself: no change
-                if (i < P.nrows) {
-                    const int2 o = htab[i];
+                if (i < qnrows) {
+                    const int2 o = qhtab[i];
                     eo[q] = right ? o.y : o.x - 1;
                     lo[q] = right ? o.x : o.y - 1;
                 }
@@ -1163,14 +1262,14 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 int d = 0;
     #pragma unroll
                 for (int q = 0; q < kRowsPerLane; ++q)
-                    if (32 * q < P.nrows) d += (int)(ctr[eo[q]] < p) - (int)(ctr[lo[q]] < p);
+                    if (32 * q < qnrows) d += (int)(ctr[eo[q]] < p) - (int)(ctr[lo[q]] < p);
                 d = __reduce_add_sync(kFull, d);
                 // targets of the pivot's window and of the next one (re-read: no extra live state)
                 const int tp = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
                 cu += right ? 1 : -1;
                 s += right ? 1 : -1;
                 const int tn = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
-                const int m = ballot_select(om, N, p, tp + d, tn, cu - cx0, cv - cy0, member);
+                const int m = ballot_select(om, Nq, p, tp + d, tn, cu - cx0, cv - cy0, qmember);
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
                 p = max(m, 0);
                 if (lane == 0) med[t * TX + s] = (uint16_t)p;
@@ -1189,7 +1288,8 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             const int groups = TX / 32;
             const int cg = warp % groups;
             const int rest = warp / groups;
-            const int band = P.vmix ? (rest + lane) % P.RB : rest % P.RB;  // per lane with mixing
+            const int vmix = XT == 1 && P.multi ? P.q_vmix[q] : P.vmix;
+            const int band = vmix ? (rest + lane) % P.RB : rest % P.RB;  // per lane with mixing
             const int down = rest / P.RB;  // 0: up, 1: down
             const int s = cg * 32 + lane;
             int t = band * BH + BH / 2;
@@ -1197,7 +1297,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             const int cu = s - xmin;
             int cv = t - ymin;
             int p = med[t * TX + s];
-            const int ncols = P.ncols;
+            const int ncols = qncols;
             const int scan_groups = P.scan_groups;
             const int eoff = down ? 0 : -SP;
             const Img im(P);
@@ -1218,13 +1318,13 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 if (down) {
     #pragma unroll 4
                     for (int j = 0; j < ncols; ++j) {
-                        const int2 o = vtab[j];
+                        const int2 o = qvtab[j];
                         d += (int)(ctr[o.y] < p) - (int)(ctr[o.x] < p);
                     }
                 } else {
     #pragma unroll 4
                     for (int j = 0; j < ncols; ++j) {
-                        const int2 o = vtab[j];
+                        const int2 o = qvtab[j];
                         d += (int)(ctr[o.x] < p) - (int)(ctr[o.y] < p);
                     }
                 }
@@ -1233,7 +1333,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 t += down ? 1 : -1;
                 const int tn = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
                 const int mine =
-                    thread_select<SHAPE, W, KS>(om, N, p, tp + d, tn, cu - cx0, cv - cy0, member, scan_groups);
+                    thread_select<SHAPE, W, KS>(om, Nq, p, tp + d, tn, cu - cx0, cv - cy0, qmember, scan_groups);
                 if (mine < 0) set_status(FIM_ERR_INTERNAL);
                 p = max(mine, 0);
                 if (pdst) *pdst = pval;  // the previous pixel's value has arrived by now
@@ -1260,6 +1360,10 @@ __device__ __forceinline__ void load_tables(const Plan& P) {
         spans[i] = P.spans[i];
     }
     for (int i = tid; i < P.SH; i += nt) frow[i] = P.frow[i];
+    if (P.xtab != nullptr) {
+        int* xt = reinterpret_cast<int*>(smem + P.off_xtab);
+        for (int i = tid; i < P.xtab_words; i += nt) xt[i] = P.xtab[i];
+    }
     if (P.off_model >= 0 && P.model != nullptr) {  // kMlpParams is even: copy 32-bit pairs
         const uint32_t* src = reinterpret_cast<const uint32_t*>(P.model);
         uint32_t* dst = reinterpret_cast<uint32_t*>(smem + P.off_model);

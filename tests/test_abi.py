@@ -118,6 +118,17 @@ def test_argument_checks_need_no_gpu():
     assert lib.fim_percentiles(a, bad, pcts, 2, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
     badp = (ctypes.c_double * 2)(50.0, -1.0)
     assert lib.fim_percentiles(a, outs, badp, 2, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
+    # several radii: count outside 1..8, null arrays, a kernel that is not a disk, an output
+    # overlapping the input
+    kk = (ctypes.c_void_p * 9)(*([k.handle] * 9))
+    for count in (0, 9):
+        assert lib.fim_median_radii(a, outs, kk, count, 4, 4, 8, fim.FIM_U16, 0, None) == INVALID
+    assert lib.fim_median_radii(a, None, kk, 2, 4, 4, 8, fim.FIM_U16, 0, None) == INVALID
+    assert lib.fim_median_radii(a, outs, None, 2, 4, 4, 8, fim.FIM_U16, 0, None) == INVALID
+    sq = fim.fim_create_kernel_spans([-1, -1, -1], [1, 1, 1], -1)
+    mixed = (ctypes.c_void_p * 2)(k.handle, sq.handle)
+    assert lib.fim_median_radii(a, outs, mixed, 2, 4, 4, 8, fim.FIM_U16, 0, None) == INVALID
+    assert lib.fim_median_radii(a, bad, kk, 2, 4, 4, 8, fim.FIM_U16, 0, None) == INVALID
     # percentile map: null, pitch below 4 * w or not a multiple of 4, overlapping the output
     m = a + 3072
     assert lib.fim_percentile_map(a, a + 2048, None, 16, 4, 4, 8, fim.FIM_U16, k.handle, 0, None) == INVALID
