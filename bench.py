@@ -182,11 +182,15 @@ def algorithmic_ops_per_pixel(r: int, footprint: int, tile_w: int, tile_h: int, 
     return footprint / (tile_w * tile_h) * passes + 2 * w + 64
 
 
-def sort_passes(dtype: str, threads: int) -> int:
-    """Key passes of the ordinal transform the library runs for a plan (see the docstring above)."""
+def sort_passes(dtype: str, threads: int, footprint: int = 0) -> int:
+    """Key passes of the ordinal transform the library runs for a plan (see the docstring above);
+    footprints beyond 65535 pixels overflow the 16-bit counters of the 65536-bin pass: 16-bit
+    data counts in two rounds, float keys take four 8-bit passes."""
     if dtype == "f32":  # full CTAs: one 16-bit counting pass + two 8-bit passes
-        return 3 if threads >= 1024 else 4
+        return 3 if threads >= 1024 and footprint <= 65535 else 4
     if dtype == "u16" and threads < 1024:
+        return 2
+    if dtype == "u16" and footprint > 65535:  # the counting sort in two rounds over the key range
         return 2
     return 1
 
@@ -304,7 +308,7 @@ SWEEP_RADII = (2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128)
 def roofline_entry(fim, kernel, code, dtype, w, h, ms, r, width, clock_mhz):
     plan = fim.fim_plan_info(kernel, code, w, h)
     ops = algorithmic_ops_per_pixel(r, plan["footprint"], plan["tile_w"], plan["tile_h"],
-                                    sort_passes(dtype, plan["threads"]), width)
+                                    sort_passes(dtype, plan["threads"], plan["footprint"]), width)
     frac = ops * w * h / (ms * 1e-3) / peak_alu_ops(clock_mhz)
     return {"ms": round(ms, 4), "Mpix_s": round(w * h / ms / 1e3, 1), "tile": f'{plan["tile_w"]}x{plan["tile_h"]}',
             "threads": plan["threads"], "footprint": plan["footprint"], "ops_per_px": round(ops, 1),
@@ -856,7 +860,7 @@ def run_native(args):
         lm = [l[i] for l in launch_ms]
         avg = sum(lm) / len(lm)
         plan = fim.fim_plan_info(kernels[i], fim.FIM_U16, W, H)
-        passes = sort_passes("u16", plan["threads"])
+        passes = sort_passes("u16", plan["threads"], plan["footprint"])
         ops = algorithmic_ops_per_pixel(r, plan["footprint"], plan["tile_w"], plan["tile_h"], passes) * H * W
         tot_ops += ops
         tot_ms += avg

@@ -39,7 +39,7 @@ int esize(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); 
 // Relative cost of one tile, used only to start the expensive tiles first.
 double tile_cost(const Plan& p) {
     const double px = (double)p.Tx * p.Ty;
-    const double sort = p.sort == kSortRadix ? 12.0 : (p.sort == kSortRadix16 ? 8.0 : 3.0);
+    const double sort = p.sort == kSortRadix ? 12.0 : (p.sort == kSortRadix16 ? 8.0 : (p.sort == kSortCount16x2 ? 6.0 : 3.0));
     return p.N * sort + px * (2.0 * p.ncols + 80.0) + (double)p.RB * p.G * p.n * 2.0;
 }
 

@@ -175,7 +175,7 @@ static int span_lo_host(int s) { return (int)(int16_t)(s & 0xffff); }
 static int elem_size(int dtype) { return dtype == FIM_U8 ? 1 : (dtype == FIM_U16 ? 2 : 4); }
 
 fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, int smem_limit,
-                     Plan* p, int cta_threads) {
+                     Plan* p, int cta_threads, bool exact_ranks) {
     memset(p, 0, sizeof(*p));
     p->dtype = dtype;
     p->w = w;
@@ -234,7 +234,15 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
         p->frow[v] = (int)((uint32_t)(fl & 0xffff) | ((uint32_t)fr << 16));
         N += fr - fl + 1;
     }
-    if (N > 65535) return FIM_ERR_UNSUPPORTED;
+    // Footprints beyond 65535 pixels keep 16-bit ordinal ranks relative to the tile's feasible
+    // median ranks [rank, N - n + rank] (Fig. 10), which is all a pivot ever takes; callers whose
+    // targets vary per pixel or per kernel (exact_ranks) need N <= 65535.
+    p->rank_base = 0;
+    if (N > 65535) {
+        if (exact_ranks || N > (1 << 20)) return FIM_ERR_UNSUPPORTED;
+        p->rank_base = std::max(0, rank - 1);
+        if (N - k->n + rank - p->rank_base > 65535) return FIM_ERR_UNSUPPORTED;
+    }
     p->N = (int)N;
     // 8-bit coordinates (u - S/2, v - SH/2) reach (-128, -128), the mark of the padding entries,
     // only at box position (0, 0) of a 256 x 256 box; they serve unless that corner belongs to the
@@ -251,6 +259,7 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     // atomic each; the walk wins where the footprint is small against the kernel (measured on the
     // 4096^2 photo-like workload: walk +1 % at r = 64, +8 % at r = 96; histogram ahead up to r = 48).
     p->seed_mode = p->N < 4 * p->n ? kSeedWalk : kSeedHistogram;
+    if (p->rank_base > 0) p->seed_mode = kSeedWalk;  // the histogram bins the ordinal image's ranks
     if (const char* e = getenv("FIM_SEEDS"))  // experiments: 0 histogram, 1 walk, 2 count at the middle
         if (*e >= '0' && *e <= '2' && e[1] == 0) p->seed_mode = *e - '0';
     for (int j = 0; j < p->ncols; ++j) {
@@ -271,6 +280,10 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     // Float keys in full CTAs: the 65536 bins sort the low half of the key in one pass, which
     // replaces two of the four 8-bit passes (the layout falls back to four when they do not fit).
     if (dtype == FIM_F32 && p->threads >= 1024) p->sort = kSortRadix16;
+    // more than 65535 footprint pixels overflow the packed 16-bit counters of the 65536 bins:
+    // 16-bit data in full CTAs counts in two rounds of 32-bit bins, float keys take 8-bit passes
+    if (p->N > 65535 && p->sort != kSortCount8)
+        p->sort = dtype == FIM_U16 && p->threads >= 1024 ? kSortCount16x2 : kSortRadix;
     // Placement. Tables, the ordinal image, medians and histograms always live in shared memory;
     // the omnigram, the radix keys and the radix position lists go to the CTA's global scratch
     // slice when shared memory cannot hold them (large kernels).
@@ -325,7 +338,7 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
         return gloc(o);
     };
     size_t smem = 0;
-    if (p->sort == kSortCount8 || p->sort == kSortCount16) {
+    if (p->sort == kSortCount8 || p->sort == kSortCount16 || p->sort == kSortCount16x2) {
         const size_t bins = p->sort == kSortCount8 ? 256 * 4 : 32768 * 4;
         const size_t uni = std::max(bins, solve_bytes);
         const bool om_smem = !p->wide && tab + om_bytes + uni <= (size_t)smem_limit;
@@ -410,14 +423,14 @@ static bool parse_tile_env(TileShape* ts) {
 }
 
 fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int w, int h,
-                       int cta_threads) {
+                       int cta_threads, bool exact_ranks) {
     static const TileShape cands[] = {{32, 32, 2, 1}, {32, 32, 4, 1}, {64, 128, 8, 2}, {64, 64, 8, 2},
                                       {32, 64, 8, 2}, {32, 32, 8, 2}, {32, 16, 8, 2}};
     TileShape forced;
     if (parse_tile_env(&forced)) {  // explicit override (experiments, tuning)
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
-        fim_status s = make_plan(k, dtype, 0, 1, 1, forced, smem_limit, p);
+        fim_status s = make_plan(k, dtype, 0, 1, 1, forced, smem_limit, p, cta_threads, exact_ranks);
         const int bytes = p->smem_bytes;
         delete p;
         if (s != FIM_OK) return s;
@@ -431,7 +444,7 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     if ((cta_threads > 0 && tuned_lookup(k, dtype, &tuned, sc, cta_threads)) || tuned_lookup(k, dtype, &tuned, sc, 0)) {
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
-        fim_status s = make_plan(k, dtype, 0, 1, 1, tuned, smem_limit, p);
+        fim_status s = make_plan(k, dtype, 0, 1, 1, tuned, smem_limit, p, cta_threads, exact_ranks);
         delete p;
         if (s == FIM_OK) {
             *ts = tuned;
@@ -445,17 +458,31 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     // beyond: taller 64x128 tiles, which halve the seed and seed-row work per pixel.
     const int extent = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1;
     const int first = extent <= 33 ? 0 : (extent <= 45 ? 1 : (extent >= 65 ? 2 : 3));
+    // A footprint beyond 65535 pixels (ranks relative to the feasible range) sorts by radix passes
+    // on global lists; an exact-rank plan keeps its sort in shared memory. The first exact-rank
+    // shape wins unless its tile is tiny (under 2048 pixels, where the per-pixel sort work
+    // explodes); then the first larger-footprint shape seen before it does (measured, 4096^2
+    // u16: r = 96 2.98 Gpix/s on 64x64 against 2.13 on 64x128; r = 128 1.04 on 64x64 against
+    // 0.21 on 32x16).
+    const TileShape* wide_choice = nullptr;
     for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
         const TileShape& c = cands[i];
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
-        fim_status s = make_plan(k, dtype, 0, 1, 1, c, smem_limit, p);
-        const int bytes = p->smem_bytes;
+        fim_status s = make_plan(k, dtype, 0, 1, 1, c, smem_limit, p, cta_threads, exact_ranks);
+        const int bytes = p->smem_bytes, n = p->N;
         delete p;
-        if (s == FIM_OK && bytes <= smem_limit) {
-            *ts = c;
-            return FIM_OK;
+        if (s != FIM_OK || bytes > smem_limit) continue;
+        if (n > 65535) {
+            if (!wide_choice) wide_choice = &c;
+            continue;
         }
+        *ts = wide_choice && c.Tx * c.Ty < 2048 ? *wide_choice : c;
+        return FIM_OK;
+    }
+    if (wide_choice) {
+        *ts = *wide_choice;
+        return FIM_OK;
     }
     return FIM_ERR_UNSUPPORTED;
 }
@@ -720,12 +747,20 @@ fim_status fim_percentiles(const void* in, void* const* outs, const double* perc
         ranks[i] = std::min(std::max((int)floor(percentiles[i] / 100.0 * (k->n - 1) + 0.5), 0), k->n - 1);
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
-    s = make_plan(k, dtype, ranks[0], w, h, ts, smem_limit, p);
+    int rmin = ranks[0], rmax = ranks[0];
+    for (int i = 1; i < count; ++i) {
+        rmin = std::min(rmin, ranks[i]);
+        rmax = std::max(rmax, ranks[i]);
+    }
+    // offset ranks (large footprints) must resolve every target's feasible ranks
+    s = make_plan(k, dtype, rmin, w, h, ts, smem_limit, p);
+    if (s == FIM_OK && p->N > 65535 && p->N - k->n + rmax - p->rank_base > 65535) s = FIM_ERR_UNSUPPORTED;
     if (s == FIM_OK) {
         p->in = in;
         p->out = outs[0];
         p->pitch = (long long)pitch_bytes;
         p->nranks = count;
+        p->rank = ranks[0];
         for (int i = 0; i < count; ++i) {
             p->ranks[i] = ranks[i];
             p->outs[i] = outs[i];
@@ -752,11 +787,12 @@ fim_status fim_median_radii(const void* in, void* const* outs, const fim_kernel*
     if (smem_limit <= 0) return FIM_ERR_CUDA;
     const fim_kernel* kb = kernels[big];
     TileShape ts;
-    fim_status s = choose_tile(kb, dtype, smem_limit, &ts, w, h);
+    // the omnigram is narrowed from disk to disk with exact ranks: no rank offsets
+    fim_status s = choose_tile(kb, dtype, smem_limit, &ts, w, h, 0, true);
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
-    s = make_plan(kb, dtype, (kb->n - 1) / 2, w, h, ts, smem_limit, p);
+    s = make_plan(kb, dtype, (kb->n - 1) / 2, w, h, ts, smem_limit, p, 0, true);
     // Targets run largest disk first, so that each footprint holds the next one and the tile can
     // narrow its omnigram from disk to disk. Every disk's tables (per-column vertical-slide
     // offsets, per-row horizontal offsets and spans) are relative to the window centre in the
@@ -863,11 +899,11 @@ fim_status fim_percentile_map(const void* in, void* out, const float* percentile
     if (smem_limit < 0) smem_limit = device_smem_limit();
     if (smem_limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    s = choose_tile(k, dtype, smem_limit, &ts, w, h);
+    s = choose_tile(k, dtype, smem_limit, &ts, w, h, 0, true);  // a rank per pixel: exact ranks
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;
-    s = make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, smem_limit, p);
+    s = make_plan(k, dtype, (k->n - 1) / 2, w, h, ts, smem_limit, p, 0, true);
     if (s == FIM_OK) {
         p->in = in;
         p->out = out;

@@ -14,7 +14,7 @@
 namespace fim {
 
 constexpr int kMaxExtent = 264;   // kernel rows / columns held in a plan (>= FIM_MAX_KERNEL_EXTENT)
-constexpr int kMaxSide = 320;     // bounding-box rows of a tile footprint held in a plan
+constexpr int kMaxSide = 400;     // bounding-box rows of a tile footprint held in a plan
 constexpr int kSortBins = 256;    // 8-bit radix digits
 constexpr int kSeedBins = 256;    // coarse histogram bins of a seed solve
 
@@ -61,8 +61,10 @@ enum SortKind : int {
     kSortCount8 = 0,   // 256-bin counting sort (8-bit data)
     kSortCount16 = 1,  // 65536-bin counting sort with packed 16-bit bins (16-bit data, Eq. 5)
     kSortRadix = 2,    // stable LSD radix sort, 8-bit passes (four for float keys, two for 16-bit data)
-    kSortRadix16 = 3   // float keys in 1024-thread CTAs: 65536-bin counting pass on the low 16 bits,
+    kSortRadix16 = 3,  // float keys in 1024-thread CTAs: 65536-bin counting pass on the low 16 bits,
                        // then two stable 8-bit passes
+    kSortCount16x2 = 4 // 16-bit data, footprints beyond 65535 pixels, 1024-thread CTAs: the counting
+                       // sort in two rounds over the key range with 32768 32-bit bins each
 };
 
 // Everything a tile kernel launch needs, passed by value as a __grid_constant__ parameter.
@@ -105,8 +107,9 @@ struct Plan {
     int off_xtab;
     // footprint
     int N;                  // pixels in the rounded-rectangle footprint
+    int rank_base;          // the ordinal image and the medians hold rank - rank_base (16 bits)
     int cx0, cy0;           // omnigram coordinates are stored as (u - cx0, v - cy0), int8 each
-    unsigned div_magic;     // ceil(2^32 / S): v = umulhi(pos, magic) for pos < 2^16 (radix path)
+    unsigned div_magic;     // ceil(2^32 / S): v = umulhi(pos, magic) = pos / S for pos < 2^32 / S (radix path)
     int hist_shift;         // seed histogram: bin = rank >> hist_shift
     int seed_mode;          // SeedMode of the plain seeds
     int sort;               // SortKind
@@ -191,14 +194,17 @@ namespace fim {
 fim_status get_scratch(cudaStream_t stream, size_t bytes, unsigned char** out);
 fim_status release_scratch();
 int device_sm_count();
+// exact_ranks: the plan's targets vary per pixel or per kernel, so its ordinal image must hold
+// exact ranks (footprints up to 65535 pixels); otherwise larger footprints hold ranks relative to
+// the feasible median ranks of `rank`.
 fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, const TileShape& ts, int smem_limit,
-                     Plan* p, int cta_threads = 0);
+                     Plan* p, int cta_threads = 0, bool exact_ranks = false);
 // Re-lays out a plan whose model is set so that the bracket MLP's parameters are staged in
 // shared memory; keeps them in device memory (off_model = -1) when they do not fit.
 fim_status plan_stage_model(Plan* p, int smem_limit);
 // Tile shape for an image of w x h (w or h <= 0: a batch, which fills the GPU like a large image).
 fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape* ts, int w, int h,
-                       int cta_threads = 0);
+                       int cta_threads = 0, bool exact_ranks = false);
 int device_smem_limit();
 
 // Autotuner cache (fim_tune.cu).

@@ -522,6 +522,55 @@ __device__ void scan_bins16(uint32_t* bins, uint32_t* wtot, const Plan& P, const
     G.sync();
 }
 
+// Block-wide exclusive scan of 32768 32-bit counters, offset by `base`; returns their total
+// (every thread). Each warp owns a contiguous chunk; each lane 4 counters (one 128-bit word) per
+// 128-counter slab.
+__device__ uint32_t scan_bins32(uint32_t* bins, uint32_t* wtot, uint32_t base, const Plan& P, const Grp& G) {
+    const int lane = G.lane, warp = G.warp;
+    const int chunk = 32768 / P.nwarps;  // counters per warp, a multiple of 128
+    uint4* b4 = reinterpret_cast<uint4*>(bins + warp * chunk);
+    uint32_t acc = 0;
+    for (int it = 0; it < chunk / 128; ++it) {
+        const uint4 q = b4[it * 32 + lane];
+        acc += q.x + q.y + q.z + q.w;
+    }
+    acc = __reduce_add_sync(kFull, acc);
+    if (lane == 0) wtot[warp] = acc;
+    G.sync();
+    if (warp == 0) {
+        const uint32_t x = lane < P.nwarps ? wtot[lane] : 0;
+        uint32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        wtot[lane] = incl - x;
+        if (lane == 31) wtot[32] = incl;
+    }
+    G.sync();
+    uint32_t run = base + wtot[warp];
+    const uint32_t total = wtot[32];
+    for (int it = 0; it < chunk / 128; ++it) {
+        uint4 q = b4[it * 32 + lane];
+        const uint32_t sum = q.x + q.y + q.z + q.w;
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint32_t b = run + incl - sum;
+        const uint32_t c0 = q.x, c1 = q.y, c2 = q.z;
+        q.x = b;
+        q.y = b + c0;
+        q.z = q.y + c1;
+        q.w = q.z + c2;
+        b4[it * 32 + lane] = q;
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    G.sync();
+    return total;
+}
+
 // The image as the tile pipeline reads it, held in registers.
 struct Img {
     const char* in;
@@ -548,13 +597,59 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
     const Img im(P);
     const int SH = P.SH, nwarps = P.nwarps, cx0 = P.cx0, cy0 = P.cy0;
     constexpr bool k16 = DT == FIM_U16;
+    constexpr int kLoads = 8;
+    if constexpr (k16) {
+        if (P.sort == kSortCount16x2) {
+            // Footprints of more than 65535 pixels: the same construction in two rounds over the
+            // key range (top bit 0, then 1), each with 32768 32-bit bins in the same 128 KiB; the
+            // second round's offsets start after the first round's pixels.
+            uint32_t base = 0;
+            for (int h = 0; h < 2; ++h) {
+                for (int i = tid * 4; i < 32768; i += P.threads * 4)
+                    *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
+                G.sync();
+                for (int v = warp; v < SH; v += nwarps) {
+                    const int fr = frow[v];
+                    const int hi = span_hi(fr);
+                    for (int u0 = span_lo(fr) + lane; u0 <= hi; u0 += 32 * kLoads) {
+                        uint32_t key[kLoads];
+#pragma unroll
+                        for (int k = 0; k < kLoads; ++k)
+                            key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v))
+                                                       : 0xffffffffu;
+#pragma unroll
+                        for (int k = 0; k < kLoads; ++k)
+                            if ((key[k] >> 15) == (uint32_t)h) atomicAdd(&bins[key[k] & 0x7fffu], 1u);
+                    }
+                }
+                G.sync();
+                base += scan_bins32(bins, misc, base, P, G);
+                for (int v = warp; v < SH; v += nwarps) {
+                    const int fr = frow[v];
+                    const int hi = span_hi(fr);
+                    for (int u0 = span_lo(fr) + lane; u0 <= hi; u0 += 32 * kLoads) {
+                        uint32_t key[kLoads];
+#pragma unroll
+                        for (int k = 0; k < kLoads; ++k)
+                            key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v))
+                                                       : 0xffffffffu;
+#pragma unroll
+                        for (int k = 0; k < kLoads; ++k)
+                            if ((key[k] >> 15) == (uint32_t)h)
+                                om[atomicAdd(&bins[key[k] & 0x7fffu], 1u)] = Loc<W>::pack(u0 + 32 * k, v, cx0, cy0);
+                    }
+                }
+                G.sync();
+            }
+            return;
+        }
+    }
     const int nwords = k16 ? 32768 : 256;
     for (int i = tid * 4; i < nwords; i += P.threads * 4)
         *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
     G.sync();
     // A warp takes one footprint row at a time; each lane loads up to kLoads pixels of it (all in
     // flight at once) before it issues their shared-memory atomics.
-    constexpr int kLoads = 8;
     for (int v = warp; v < SH; v += nwarps) {
         const int fr = frow[v];
         const int hi = span_hi(fr);
@@ -982,6 +1077,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     const int gx0 = tx0 + P.xmin;  // global coordinates of bounding-box pixel (0, 0)
     const int gy0 = ty0 + P.ymin;
     const int cx0 = P.cx0, cy0 = P.cy0, xmin = P.xmin, ymin = P.ymin, hist_shift = P.hist_shift;
+    // The ordinal image and the medians hold ranks minus rank_base, clamped to 16 bits: every
+    // pivot lies in the tile's feasible median ranks (Fig. 10), which then compare exactly, so
+    // footprints beyond 65535 pixels keep a 16-bit ordinal image (rank_base = 0 below that).
+    const int rb = P.rank_base;
 
     const int2* vtab = reinterpret_cast<const int2*>(smem_base + P.off_vtab);
     const int2* htab = reinterpret_cast<const int2*>(smem_base + P.off_htab);
@@ -1026,7 +1125,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     stamp(P, tile, 2, G);
     for (int v = tid; v < N; v += nthreads) {
         const uint32_t e = om[v];
-        ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)v;
+        ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)clampi(v - rb, 0, 65535);
     }
     {   // pad the last 128-bit group with sentinels no window contains
         const int pad = ((N + Loc<W>::kGroup - 1) & ~(Loc<W>::kGroup - 1)) - N;
@@ -1162,14 +1261,15 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 const float span = (float)(hif - lof);
                 const int lo = clampi(__float2int_rn(lof + (o0 - sig) * span), 0, Nq - 1);
                 const int hi = clampi(__float2int_rn(lof + (o0 + sig) * span), lo, Nq - 1);
-                const int pivot = clampi(__float2int_rn(lof + o0 * span), lo, hi);
+                // (pivots stay in the feasible ranks, where the ordinal image's ranks compare exactly)
+                const int pivot = clampi(clampi(__float2int_rn(lof + o0 * span), lo, hi), lof, hif);
                 // The count at the predicted median is exact, so the walk from it finds the exact
                 // median wherever it lies: on a miss it simply walks past the bracket, over the
                 // full range if need be. The bracket ends only classify the outcome.
-                const int below = window_rows_below(qspans, qnrows, ord + (cv + qymin) * SP + cu, SP, pivot);
+                const int below = window_rows_below(qspans, qnrows, ord + (cv + qymin) * SP + cu, SP, pivot - rb);
                 const int m = wide_select<SHAPE, W>(om, Nq, pivot, below, target, cu - cx0, cv - cy0, qmember);
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
-                if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+                if (lane == 0) med[t * TX + s] = (uint16_t)(max(m, 0) - rb);
                 if (counting && lane == 0) {
                     const int kind = m < lo ? 2 : (m > hi ? 3 : 1);
                     atomicAdd(P.stats + 0, 1ull);
@@ -1208,12 +1308,12 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                     } else {
                         // count the window below the middle of the tile's feasible ranks, walk from there
                         pivot = (lof + hif) >> 1;
-                        below = window_rows_below(qspans, qnrows, ord + (cv + qymin) * SP + cu, SP, pivot);
+                        below = window_rows_below(qspans, qnrows, ord + (cv + qymin) * SP + cu, SP, pivot - rb);
                     }
                     m = wide_select<SHAPE, W>(om, Nq, pivot, below, ts, cu - cx0, cv - cy0, qmember);
                 }
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
-                if (lane == 0) med[t * TX + s] = (uint16_t)max(m, 0);
+                if (lane == 0) med[t * TX + s] = (uint16_t)(max(m, 0) - rb);
                 if (sampling) {  // training row: features and the exact median's place in [lof, hif]
                     unsigned int row = 0;
                     if (lane == 0) row = atomicAdd(P.sample_count, 1u);
@@ -1244,7 +1344,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             const int steps = right ? (GW - GW / 2 - 1) : (GW / 2);
             int cu = s - xmin;
             const int cv = t - ymin;
-            int p = med[t * TX + s];
+            int p = med[t * TX + s] + rb;
             constexpr int kRowsPerLane = (kMaxExtent + 31) / 32;
             int eo[kRowsPerLane], lo[kRowsPerLane];  // this lane's rows: entering / leaving offsets
     #pragma unroll
@@ -1259,10 +1359,11 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             }
             for (int k = 0; k < steps; ++k) {
                 const uint16_t* ctr = ord + cv * SP + cu;
+                const int pr = p - rb;  // the pivot among the ordinal image's ranks
                 int d = 0;
     #pragma unroll
                 for (int q = 0; q < kRowsPerLane; ++q)
-                    if (32 * q < qnrows) d += (int)(ctr[eo[q]] < p) - (int)(ctr[lo[q]] < p);
+                    if (32 * q < qnrows) d += (int)(ctr[eo[q]] < pr) - (int)(ctr[lo[q]] < pr);
                 d = __reduce_add_sync(kFull, d);
                 // targets of the pivot's window and of the next one (re-read: no extra live state)
                 const int tp = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
@@ -1272,7 +1373,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 const int m = ballot_select(om, Nq, p, tp + d, tn, cu - cx0, cv - cy0, qmember);
                 if (m < 0) set_status(FIM_ERR_INTERNAL);
                 p = max(m, 0);
-                if (lane == 0) med[t * TX + s] = (uint16_t)p;
+                if (lane == 0) med[t * TX + s] = (uint16_t)(p - rb);
             }
         }
         G.sync();
@@ -1296,7 +1397,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             const int steps = down ? (BH - BH / 2 - 1) : (BH / 2);
             const int cu = s - xmin;
             int cv = t - ymin;
-            int p = med[t * TX + s];
+            int p = med[t * TX + s] + rb;
             const int ncols = qncols;
             const int scan_groups = P.scan_groups;
             const int eoff = down ? 0 : -SP;
@@ -1314,18 +1415,19 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
             if (down) gather(p, t);  // the seed row's pixel
             for (int k = 0; k < steps; ++k) {
                 const uint16_t* ctr = ord + cv * SP + cu + eoff;
+                const int pr = p - rb;  // the pivot among the ordinal image's ranks
                 int d = 0;
                 if (down) {
     #pragma unroll 4
                     for (int j = 0; j < ncols; ++j) {
                         const int2 o = qvtab[j];
-                        d += (int)(ctr[o.y] < p) - (int)(ctr[o.x] < p);
+                        d += (int)(ctr[o.y] < pr) - (int)(ctr[o.x] < pr);
                     }
                 } else {
     #pragma unroll 4
                     for (int j = 0; j < ncols; ++j) {
                         const int2 o = qvtab[j];
-                        d += (int)(ctr[o.x] < p) - (int)(ctr[o.y] < p);
+                        d += (int)(ctr[o.x] < pr) - (int)(ctr[o.y] < pr);
                     }
                 }
                 const int tp = mapped ? map_rank(P, tx0 + s, ty0 + t) : target;
