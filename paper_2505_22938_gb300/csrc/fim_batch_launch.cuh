@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(1024, 1) batch_class_kernel(const __grid_const
             cur = job;
         }
         const Plan& P = *reinterpret_cast<const Plan*>(s_plan);
-        process_tile<DT, SHAPE, W, OG, KS>(P, t - __ldg(A.tile_start + job), gslice, G);
+        process_tile<DT, SHAPE, W, OG, KS, 0, false>(P, t - __ldg(A.tile_start + job), gslice, G);
     }
 }
 

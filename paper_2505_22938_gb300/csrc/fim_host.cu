@@ -160,6 +160,52 @@ fim_status release_scratch() {
     return FIM_OK;
 }
 
+int device_smem_per_sm() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+namespace {
+// cuTensorMapEncodeTiled from the driver, found through the runtime (no driver library link)
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &f, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(f);
+        cudaGetLastError();
+    });
+    return fn;
+}
+}  // namespace
+
+void attach_tma(Plan& p) {
+    p.use_tma = 0;
+    if (p.loc_stage < 0 || getenv("FIM_NO_TMA")) return;
+    if (((uintptr_t)p.in & 15) != 0 || (p.pitch & 15) != 0) return;
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return;
+    const CUtensorMapDataType t = p.dtype == FIM_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                  : (p.dtype == FIM_U16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+    const cuuint64_t dims[2] = {(cuuint64_t)p.w, (cuuint64_t)p.h};
+    const cuuint64_t strides[1] = {(cuuint64_t)p.pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)p.stage_bw, (cuuint32_t)p.SH};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&p.tmap, t, 2, const_cast<void*>(p.in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        p.use_tma = 1;
+}
+
 int device_smem_limit() {
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -406,6 +452,30 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
         smem = std::max(off, uni + solve_bytes);
     }
     if (smem > (size_t)smem_limit) return FIM_ERR_UNSUPPORTED;
+    // Staging region for the footprint copies of interior tiles (128 bytes of slack let the kernel
+    // align it to 128 bytes): only where the box is a valid copy (at most 256 x 256 elements, rows
+    // a multiple of 16 bytes) and the region fits beside everything else without costing the SM a
+    // resident CTA.
+    p->loc_stage = -1;
+    p->stage_bw = 0;
+    p->use_tma = 0;
+    {
+        const int es = elem_size(p->dtype), A = 16 / es;
+        const int bw = (p->S + A - 1 + A - 1) / A * A;
+        const size_t off = (smem + 127) & ~(size_t)127;
+        const size_t end = off + (size_t)bw * p->SH * es + 128;
+        const int per_sm = device_smem_per_sm();
+        auto ctas = [&](size_t bytes) {  // resident CTAs per SM by shared memory and registers
+            const int by_regs = 65536 / (p->threads * 64);
+            return per_sm > 0 ? std::min(by_regs, per_sm / (int)(align16(bytes) + 1024)) : 0;
+        };
+        if (bw <= 256 && p->SH <= 256 && end <= (size_t)smem_limit && per_sm > 0 && ctas(end) >= ctas(smem) &&
+            ctas(end) >= 1) {
+            p->loc_stage = (int)off;
+            p->stage_bw = bw;
+            smem = end;
+        }
+    }
     p->smem_bytes = (int)align16(smem);
     p->group_bytes = p->smem_bytes - p->tab_bytes;
     p->groups = 1;

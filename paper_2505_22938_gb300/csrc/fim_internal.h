@@ -1,6 +1,7 @@
 // Internal declarations shared by the host and device translation units of libfim.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the footprint copies' tensor maps)
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -123,6 +124,10 @@ struct Plan {
     int sample_cap;                   // capacity of samples in rows
     // spatially varying percentile (extras kernels; null = every pixel takes `rank`)
     const int* rank_map;              // one target rank per output pixel, w x h, dense rows
+    // footprint staging by the tensor memory accelerator (single-image launches; set at launch)
+    int use_tma;                      // 1: interior tiles copy their footprint box into loc_stage
+    int stage_bw;                     // staged row length in elements (a multiple of 16 bytes)
+    int loc_stage;                    // shared-memory offset of the staging region (-1: none)
     unsigned long long* phase_clock;  // optional: 8 clock64() stamps per tile (diagnostics)
     int phase_tiles;                  // capacity of phase_clock in tiles
     // Array placement. A location >= 0 is a byte offset into dynamic shared memory; a location
@@ -148,6 +153,8 @@ struct Plan {
     int vtab[2 * kMaxExtent];             // per column j: top*SP + dx, (bot+1)*SP + dx
     int htab[2 * kMaxExtent];             // per row i: dy*SP + lo, dy*SP + hi + 1
     int spans[kMaxExtent];                // per row i: (lo & 0xffff) | (hi << 16)
+    // tensor map of the input image for the footprint copies (valid when use_tma)
+    alignas(64) CUtensorMap tmap;
 };
 
 // Bytes of a Plan before its tables: all the tile pipeline reads once the tables are in
@@ -225,6 +232,10 @@ void tile_candidates(std::vector<TileShape>* out);
 // Diagnostics: device buffer that receives per-phase clock64() stamps (may be null).
 void set_phase_clock_buffer(unsigned long long* buf, int tiles);
 void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
+
+// Encodes the tensor map of the plan's input image for the footprint copies when the plan has a
+// staging region and the image allows them (16-byte aligned base and pitch); sets use_tma.
+void attach_tma(Plan& p);
 
 // Device launch (fim_tile.cu).
 fim_status launch_tile_kernel(Plan& p, cudaStream_t stream);

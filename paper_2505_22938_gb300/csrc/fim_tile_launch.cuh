@@ -18,13 +18,19 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
     load_tables(P);
     unsigned int* counter = reinterpret_cast<unsigned int*>(P.scratch);
     const Grp G{tid, tid & 31, tid >> 5, (int)blockDim.x, 0, 0};
+    // the footprint copies' mbarrier (scan scratch words 34-35), initialised before the first tile
+    TmaState tma{0u, 0};
+    if (P.use_tma && tid == 0) {
+        extern __shared__ __align__(16) unsigned char smem_dyn[];
+        mbar_init(reinterpret_cast<uint64_t*>(smem_dyn + P.off_misc + 34 * 4));
+    }
     for (;;) {
         if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
         __syncthreads();
         const int tile = s_tile;
         if (tile >= P.ntiles) break;
         stamp(P, tile, 0, G);
-        process_tile<DT, SHAPE, W, OG, KS, XT>(P, P.tile0 + tile, gslice, G);
+        process_tile<DT, SHAPE, W, OG, KS, XT>(P, P.tile0 + tile, gslice, G, &tma);
     }
 }
 
@@ -48,6 +54,7 @@ fim_status launch_typed(Plan& p, cudaStream_t stream) {
     fim_status s = get_scratch(stream, 256 + (size_t)grid * (size_t)p.scratch_per_cta, &scratch);
     if (s != FIM_OK) return s;
     p.scratch = scratch;
+    attach_tma(p);
     if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;
     fn<<<grid, p.threads, p.smem_bytes, stream>>>(p);
     if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;
@@ -76,6 +83,7 @@ fim_status launch_typed_fixed(Plan& p, unsigned char* scratch, size_t capacity, 
     if (256 + (unsigned long long)grid * (unsigned long long)p.scratch_per_cta > capacity) return FIM_ERR_UNSUPPORTED;
     if (!launch) return FIM_OK;
     p.scratch = scratch;
+    attach_tma(p);
     if (cudaMemsetAsync(scratch, 0, 16, stream) != cudaSuccess) return FIM_ERR_CUDA;  // tile queue counter
     fn<<<grid, p.threads, p.smem_bytes, stream>>>(p);
     if (cudaGetLastError() != cudaSuccess) return FIM_ERR_CUDA;

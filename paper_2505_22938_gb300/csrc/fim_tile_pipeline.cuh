@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fim_internal.h"
 
@@ -587,14 +588,77 @@ __device__ __forceinline__ typename Traits<DT>::T load_px(const Img& im, int gx,
     return __ldg(row + clampi(gx, 0, im.w - 1));
 }
 
+// Where phase 1 reads the footprint from: the box staged in shared memory by the tensor memory
+// accelerator (interior tiles), or the image in global memory with clamp-to-edge (every other
+// tile). `off` is the staged column of box column 0 (the copy starts on a 16-byte boundary).
+// STAGED is fixed per call (the sorts are compiled for both), so the loads of the global-memory
+// form stay free of a per-pixel branch.
+template <int DT>
+struct Footprint {
+    using V = typename Traits<DT>::T;
+    const unsigned char* stage;  // null: read the image
+    int pitch;                   // bytes per staged row
+    int off;
+    Img im;
+    int gx0, gy0;
+    template <bool STAGED>
+    __device__ __forceinline__ uint32_t key(int u, int v) const {
+        if constexpr (STAGED) return Traits<DT>::key(reinterpret_cast<const V*>(stage + v * pitch)[u + off]);
+        else return Traits<DT>::key(load_px<DT>(im, gx0 + u, gy0 + v));
+    }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// mbarrier of the footprint copies: one arrival (the issuing thread) plus the copy's bytes.
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Copies the box of `rows` x `cols` elements at image column x0 (a multiple of 16 bytes) and row
+// y0 into shared memory at dst, completing on `bar` (issued by one thread).
+__device__ __forceinline__ void tma_load_box(const void* tmap, unsigned char* dst, uint64_t* bar, int x0, int y0,
+                                             uint32_t bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x0), "r"(y0), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Waits for phase `parity` of `bar` to complete; gives up (false) after a bounded number of tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    for (int i = 0; i < (1 << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// State of the footprint copies of one CTA across its tiles.
+struct TmaState {
+    uint32_t parity;  // phase of the next copy's completion
+    int off;          // 1 once a copy timed out: global loads from then on
+};
+
 // Counting-sort ordinal transform for 8/16-bit data (Sec. 4.1, Eq. 5): histogram of the
 // footprint, exclusive prefix, then every pixel takes the next free ordinal of its value.
 // Ties get consecutive ordinals in arrival order, which is all the method needs.
-template <int DT, int W>
+template <int DT, int W, bool STAGED>
 __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t* bins, uint32_t* misc,
-                                        typename Loc<W>::E* om, int gx0, int gy0, const Grp& G) {
+                                        typename Loc<W>::E* om, const Footprint<DT>& fp, const Grp& G) {
     const int tid = G.tid, lane = G.lane, warp = G.warp;
-    const Img im(P);
     const int SH = P.SH, nwarps = P.nwarps, cx0 = P.cx0, cy0 = P.cy0;
     constexpr bool k16 = DT == FIM_U16;
     constexpr int kLoads = 8;
@@ -615,8 +679,7 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
                         uint32_t key[kLoads];
 #pragma unroll
                         for (int k = 0; k < kLoads; ++k)
-                            key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v))
-                                                       : 0xffffffffu;
+                            key[k] = u0 + 32 * k <= hi ? fp.template key<STAGED>(u0 + 32 * k, v) : 0xffffffffu;
 #pragma unroll
                         for (int k = 0; k < kLoads; ++k)
                             if ((key[k] >> 15) == (uint32_t)h) atomicAdd(&bins[key[k] & 0x7fffu], 1u);
@@ -631,8 +694,7 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
                         uint32_t key[kLoads];
 #pragma unroll
                         for (int k = 0; k < kLoads; ++k)
-                            key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v))
-                                                       : 0xffffffffu;
+                            key[k] = u0 + 32 * k <= hi ? fp.template key<STAGED>(u0 + 32 * k, v) : 0xffffffffu;
 #pragma unroll
                         for (int k = 0; k < kLoads; ++k)
                             if ((key[k] >> 15) == (uint32_t)h)
@@ -657,7 +719,7 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
             uint32_t key[kLoads];
 #pragma unroll
             for (int k = 0; k < kLoads; ++k)
-                key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v)) : 0u;
+                key[k] = u0 + 32 * k <= hi ? fp.template key<STAGED>(u0 + 32 * k, v) : 0u;
 #pragma unroll
             for (int k = 0; k < kLoads; ++k) {
                 if (u0 + 32 * k > hi) break;
@@ -700,7 +762,7 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
             uint32_t key[kLoads];
 #pragma unroll
             for (int k = 0; k < kLoads; ++k)
-                key[k] = u0 + 32 * k <= hi ? Traits<DT>::key(load_px<DT>(im, gx0 + u0 + 32 * k, gy0 + v)) : 0u;
+                key[k] = u0 + 32 * k <= hi ? fp.template key<STAGED>(u0 + 32 * k, v) : 0u;
 #pragma unroll
             for (int k = 0; k < kLoads; ++k) {
                 if (u0 + 32 * k > hi) break;
@@ -726,15 +788,14 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
 // exclusive offset plus its position among equal digits earlier in the segment (warp match).
 // Histograms are laid out warp-major with a pad word so that the leaders of one warp never share
 // a bank. The sorted positions end in list B, which is then rewritten in place as the omnigram.
-template <int DT, int W, bool C16 = false>
+template <int DT, int W, bool C16, bool STAGED>
 __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t* keys, typename Loc<W>::Pos* bufA,
                                         typename Loc<W>::Pos* bufB, uint32_t* hist, uint32_t* wsum, uint32_t* bins,
-                                        int gx0, int gy0, const Grp& G) {
+                                        const Footprint<DT>& fp, const Grp& G) {
     using Pos = typename Loc<W>::Pos;
     const int tid = G.tid, lane = G.lane, warp = G.warp;
     const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
     constexpr int HS = kSortBins + 1;
-    const Img im(P);
     const int area = S * P.SH;
     uint32_t* hw = hist + warp * HS;
     // Exclusive scan of the per-warp digit counts in (digit, warp) order, in place: each thread
@@ -803,7 +864,7 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
             key[k] = 0;
             if (in[k]) {
                 const int v = (int)__umulhi((unsigned)i, P.div_magic);
-                key[k] = Traits<DT>::key(load_px<DT>(im, gx0 + i - v * S, gy0 + v));
+                key[k] = fp.template key<STAGED>(i - v * S, v);
             }
         }
 #pragma unroll
@@ -1060,8 +1121,11 @@ __device__ int compact_omnigram(typename Loc<W>::E* om, int N, const int* qfrow,
 // several target ranks per launch — and 2 a target rank per output pixel (a percentile map).
 // Each lives in kernels of its own: at the 64-register cap of 1024-thread CTAs their code
 // changes how the compiler allocates the plain pipeline's registers, and the reverse.
-template <int DT, int SHAPE, int W, int OG, int KS = 0, int XT = 0>
-__device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G) {
+// TMA: the footprint copies are compiled in (the single-image kernels, whose plan is a kernel
+// parameter the copies can name; the batch kernels read their plans from shared memory).
+template <int DT, int SHAPE, int W, int OG, int KS = 0, int XT = 0, bool TMA = true>
+__device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G,
+                                             TmaState* tma = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_base[];
     unsigned char* const smem = smem_base + G.shift;  // this group's partition (tables excluded)
     using V = typename Traits<DT>::T;
@@ -1096,29 +1160,69 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
 
     // ---- 1. ordinal transform ------------------------------------------------------------------
     stamp(P, tile, 1, G);
+    // The footprint: for an interior tile with a staging region, one thread has the tensor memory
+    // accelerator copy the whole box (from the 16-byte boundary at or left of its first column)
+    // into shared memory, and every thread waits on the mbarrier (bounded: after a timeout the
+    // tile, and the CTA's later tiles, read the image instead).
+    Footprint<DT> fp{nullptr, 0, 0, Img(P), gx0, gy0};
+    if (TMA && tma != nullptr && P.use_tma && !tma->off) {
+        constexpr int A = 16 / (int)sizeof(V);  // elements per 16 bytes
+        const int x0 = gx0 & ~(A - 1);
+        if (x0 >= 0 && gy0 >= 0 && x0 + P.stage_bw <= P.w && gy0 + P.SH <= P.h) {
+            unsigned char* st = smem + P.loc_stage;
+            st += (128u - (smem_addr(st) & 127u)) & 127u;  // the region has 128 bytes of slack
+            uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 34);
+            if (tid == 0)
+                tma_load_box(&P.tmap, st, bar, x0, gy0, (uint32_t)(P.stage_bw * P.SH * (int)sizeof(V)));
+            const bool ok = mbar_wait(bar, tma->parity) || mbar_wait(bar, tma->parity);
+            tma->parity ^= 1u;
+            if (ok) {
+                fp.stage = st;
+                fp.pitch = P.stage_bw * (int)sizeof(V);
+                fp.off = gx0 - x0;
+            } else {
+                tma->off = 1;
+                set_status(FIM_ERR_TIMEOUT);
+            }
+        }
+    }
     // float data always takes the radix sort; 16-bit data takes it in small CTAs, where the
     // counting sort's 65536 bins would keep other CTAs off the SM
-    if constexpr (DT == FIM_F32) {
-        if (P.sort == kSortRadix16)
-            ordinal_transform_radix<DT, W, true>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
-                                                 place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
-                                                 place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
-                                                 reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc,
-                                                 reinterpret_cast<uint32_t*>(smem + P.loc_bins), gx0, gy0, G);
+    // the sort, compiled for the staged box and for the image (one branch per tile)
+    auto sort = [&](auto staged) {
+        constexpr bool ST = decltype(staged)::value;
+        if constexpr (DT == FIM_F32) {
+            if (P.sort == kSortRadix16)
+                ordinal_transform_radix<DT, W, true, ST>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
+                                                         place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
+                                                         place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
+                                                         reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc,
+                                                         reinterpret_cast<uint32_t*>(smem + P.loc_bins), fp, G);
+            else
+                ordinal_transform_radix<DT, W, false, ST>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
+                                                          place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
+                                                          place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
+                                                          reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc,
+                                                          nullptr, fp, G);
+        } else if (DT == FIM_U16 && P.sort == kSortRadix) {
+            ordinal_transform_radix<DT, W, false, ST>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
+                                                      place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
+                                                      place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
+                                                      reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, nullptr,
+                                                      fp, G);
+        } else {
+            ordinal_transform_count<DT, W, ST>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), misc, om, fp,
+                                               G);
+        }
+    };
+    if constexpr (TMA) {
+        if (fp.stage != nullptr)
+            sort(std::true_type{});
         else
-            ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
-                                           place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
-                                           place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
-                                           reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, nullptr, gx0, gy0,
-                                           G);
-    } else if (DT == FIM_U16 && P.sort == kSortRadix)
-        ordinal_transform_radix<DT, W>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
-                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
-                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
-                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, nullptr, gx0, gy0, G);
-    else if constexpr (DT != FIM_F32)
-        ordinal_transform_count<DT, W>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), misc, om, gx0, gy0,
-                                       G);
+            sort(std::false_type{});
+    } else {
+        sort(std::false_type{});
+    }
     G.sync();
 
     // ---- 2. ordinal image I (Eq. 4) ------------------------------------------------------------
