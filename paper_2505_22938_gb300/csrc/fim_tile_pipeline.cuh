@@ -881,18 +881,35 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     // the first pass's result goes to the list the stable passes start from: with C16 two stable
     // passes follow (B -> A -> B), otherwise an odd number (A -> B -> ... -> B)
     Pos* first = C16 ? bufB : bufA;
-    if constexpr (C16) {
+    // The keys may live in global scratch: every loop below loads kG of them (all in flight)
+    // before it uses the first.
+    constexpr int kG = 4;
+    if constexpr (C16)
         scan_bins16(bins, wsum, P, G);
-        for (int i = tid; i < area; i += nthreads)
-            if (inside(i)) {
-                const uint32_t k = keys[i] & 0xffffu, sh = (k & 1u) << 4;
-                first[(atomicAdd(&bins[k >> 1], 1u << sh) >> sh) & 0xffffu] = (Pos)i;
-            }
-    } else {
+    else {
         scan_counts();
         G.sync();
-        for (int i = tid; i < area; i += nthreads)
-            if (inside(i)) first[atomicAdd(&hw[keys[i] & 0xff], 1u)] = (Pos)i;
+    }
+    for (int i0 = tid; i0 < area; i0 += kG * nthreads) {
+        uint32_t key[kG];
+        bool in[kG];
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+            const int i = i0 + k * nthreads;
+            in[k] = i < area && inside(i);
+            key[k] = in[k] ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kG; ++k)
+            if (in[k]) {
+                const int i = i0 + k * nthreads;
+                if constexpr (C16) {
+                    const uint32_t d = key[k] & 0xffffu, sh = (d & 1u) << 4;
+                    first[(atomicAdd(&bins[d >> 1], 1u << sh) >> sh) & 0xffffu] = (Pos)i;
+                } else {
+                    first[atomicAdd(&hw[key[k] & 0xff], 1u)] = (Pos)i;
+                }
+            }
     }
     G.sync();
     // stable passes over the current order: each warp owns one contiguous segment; a pixel's
@@ -910,25 +927,45 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
         const int shift = kBits0 + 8 * pass;
         for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
         __syncwarp();
-        for (int i = s0 + lane; i < s1; i += 32)  // counts do not depend on the order
-            atomicAdd(&hw[(keys[src[i]] >> shift) & 0xff], 1u);
+        for (int i0 = s0 + lane; i0 < s1; i0 += 32 * kG) {  // counts do not depend on the order
+            uint32_t key[kG];
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                const int i = i0 + 32 * k;
+                key[k] = i < s1 ? keys[src[i]] : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kG; ++k)
+                if (i0 + 32 * k < s1) atomicAdd(&hw[(key[k] >> shift) & 0xff], 1u);
+        }
         G.sync();
         scan_counts();
         G.sync();
-        for (int b = s0; b < s1; b += 32) {
-            const int i = b + lane;
-            const bool valid = i < s1;
-            const int pos = valid ? (int)src[i] : 0;
-            const int d = valid ? (int)(keys[pos] >> shift) & 0xff : kSortBins + lane;
-            const uint32_t peers = __match_any_sync(kFull, d);
-            uint32_t base = 0;
-            if (valid) base = hw[d];
-            __syncwarp();
-            if (valid) {
-                dst[base + __popc(peers & lanemask_lt())] = (Pos)pos;
-                if (lane == __ffs(peers) - 1) hw[d] = base + __popc(peers);
+        for (int b0 = s0; b0 < s1; b0 += 32 * kG) {
+            int pos[kG], d[kG];
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                const int i = b0 + 32 * k + lane;
+                pos[k] = i < s1 ? (int)src[i] : -1;
             }
-            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < kG; ++k)
+                d[k] = pos[k] >= 0 ? (int)(keys[pos[k]] >> shift) & 0xff : kSortBins + lane;
+            // batches in segment order, so equal digits keep their order
+#pragma unroll
+            for (int k = 0; k < kG; ++k) {
+                if (b0 + 32 * k >= s1) break;
+                const bool valid = pos[k] >= 0;
+                const uint32_t peers = __match_any_sync(kFull, d[k]);
+                uint32_t base = 0;
+                if (valid) base = hw[d[k]];
+                __syncwarp();
+                if (valid) {
+                    dst[base + __popc(peers & lanemask_lt())] = (Pos)pos[k];
+                    if (lane == __ffs(peers) - 1) hw[d[k]] = base + __popc(peers);
+                }
+                __syncwarp();
+            }
         }
         G.sync();
         src = dst;
