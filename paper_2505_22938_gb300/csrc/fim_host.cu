@@ -377,6 +377,7 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
     tab += 256;
     auto gloc = [](size_t off) { return -(int)off - 1; };
     p->loc_bins = p->loc_keys = p->loc_a = p->loc_b = p->loc_hist = 0;
+    p->loc_dig = -1;
     size_t glob = 0;
     auto take_glob = [&](size_t bytes) {
         const size_t o = glob;
@@ -402,18 +403,25 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
         smem = off + uni;
     } else {
         const size_t keys_bytes = align16((size_t)p->S * p->SH * 4);
+        const size_t dig_bytes = align16((size_t)p->S * p->SH);
         const size_t hist_bytes = align16((size_t)p->nwarps * (kSortBins + 1) * 4);
-        // try: everything in shared memory; keys in global; keys and lists in global. The 16-bit
-        // first pass's bins alias list A and the histograms, which are only used after it.
+        // try: (0) everything in shared memory; (1) keys in global; (2) keys and both lists in
+        // global. Float keys in (1) and (2) keep list A in global memory too and give the stable
+        // passes their digit of every box position in a shared byte array: two stable passes
+        // gathering keys from L2 one at a time made the whole sort cost 1.8x as much (f32 r = 64:
+        // 429k against 233k cycles per tile). 16-bit data (one stable pass, small footprints)
+        // keeps the gathers. The 16-bit first pass's bins alias the region of list A (or the
+        // digits) and the histograms, which are only used after it.
+        const bool use_dig = p->dtype == FIM_F32;
         int mode = 0;
         for (;;) {
             const size_t bins_bytes = p->sort == kSortRadix16 ? 32768 * 4 : 0;
             for (mode = 0; mode < 3; ++mode) {
                 if (mode < 2 && p->wide) continue;  // 32-bit lists of a wide box never fit
                 size_t need = tab;
-                if (mode < 2) need += om_bytes;       // B / omnigram
-                const size_t sort_part =
-                    (mode == 0 ? keys_bytes : 0) + std::max((mode < 2 ? om_bytes : 0) + hist_bytes, bins_bytes);
+                if (mode < 2) need += om_bytes;  // B / omnigram
+                const size_t list_a = mode == 0 ? om_bytes : (use_dig ? dig_bytes : (mode == 1 ? om_bytes : 0));
+                const size_t sort_part = (mode == 0 ? keys_bytes : 0) + std::max(list_a + hist_bytes, bins_bytes);
                 need += std::max(sort_part, solve_bytes);
                 if (need <= (size_t)smem_limit) break;
             }
@@ -436,13 +444,18 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
         } else {
             p->loc_keys = take_glob(keys_bytes);
         }
-        if (mode < 2) {
+        if (mode == 0 || (mode == 1 && !use_dig)) {
             p->loc_a = (int)off;
             off += om_bytes;
+            p->loc_bins = p->loc_a;  // start of list A's and the histograms' region
         } else {
             p->loc_a = take_glob(om_bytes);
+            p->loc_bins = (int)off;  // start of the digits' (if any) and the histograms' region
+            if (use_dig) {
+                p->loc_dig = (int)off;
+                off += dig_bytes;
+            }
         }
-        p->loc_bins = p->loc_a >= 0 ? p->loc_a : (int)off;  // start of list A's and the histograms' region
         p->loc_hist = (int)off;
         off += hist_bytes;
         if (p->sort == kSortRadix16) off = std::max(off, (size_t)p->loc_bins + 32768 * 4);

@@ -141,6 +141,7 @@ struct Plan {
     int loc_om;                                     // omnigram (from the end of the sort on)
     int loc_bins;                                   // counting sorts: bins
     int loc_keys, loc_a, loc_b, loc_hist;           // radix sort: keys, ping-pong lists, histograms
+    int loc_dig;                                    // radix sort with keys in global scratch: digit bytes (-1: none)
     int loc_ord, loc_med, loc_shist;                // solve: ordinal image, medians, seed histograms
     int smem_bytes;
     long long scratch_per_cta;  // bytes of global scratch per resident CTA (multiple of 256)

@@ -787,11 +787,14 @@ __device__ void ordinal_transform_count(const Plan& P, const int* frow, uint32_t
 // contiguous segment of the current order, and a pixel's new place is its (digit, warp)-major
 // exclusive offset plus its position among equal digits earlier in the segment (warp match).
 // Histograms are laid out warp-major with a pad word so that the leaders of one warp never share
-// a bank. The sorted positions end in list B, which is then rewritten in place as the omnigram.
+// a bank. Where the keys live in global scratch (large footprints), each stable pass first copies
+// its digit of every box position into a shared byte array (`dig`, coalesced reads of the keys),
+// so that the passes look digits up in shared memory instead of gathering keys from L2 one by one.
+// The sorted positions end in list B, which is then rewritten in place as the omnigram.
 template <int DT, int W, bool C16, bool STAGED>
 __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t* keys, typename Loc<W>::Pos* bufA,
                                         typename Loc<W>::Pos* bufB, uint32_t* hist, uint32_t* wsum, uint32_t* bins,
-                                        const Footprint<DT>& fp, const Grp& G) {
+                                        uint8_t* dig, const Footprint<DT>& fp, const Grp& G) {
     using Pos = typename Loc<W>::Pos;
     const int tid = G.tid, lane = G.lane, warp = G.warp;
     const int nthreads = P.threads, nwarps = P.nwarps, S = P.S;
@@ -923,53 +926,80 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     const int N = P.N;
     const int seg = ((N + nwarps - 1) / nwarps + 31) & ~31;
     const int s0 = min(N, warp * seg), s1 = min(N, s0 + seg);
-    for (int pass = 0; pass < kPasses; ++pass) {
-        const int shift = kBits0 + 8 * pass;
-        for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
-        __syncwarp();
-        for (int i0 = s0 + lane; i0 < s1; i0 += 32 * kG) {  // counts do not depend on the order
-            uint32_t key[kG];
-#pragma unroll
-            for (int k = 0; k < kG; ++k) {
-                const int i = i0 + 32 * k;
-                key[k] = i < s1 ? keys[src[i]] : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < kG; ++k)
-                if (i0 + 32 * k < s1) atomicAdd(&hw[(key[k] >> shift) & 0xff], 1u);
-        }
-        G.sync();
-        scan_counts();
-        G.sync();
-        for (int b0 = s0; b0 < s1; b0 += 32 * kG) {
-            int pos[kG], d[kG];
-#pragma unroll
-            for (int k = 0; k < kG; ++k) {
-                const int i = b0 + 32 * k + lane;
-                pos[k] = i < s1 ? (int)src[i] : -1;
-            }
-#pragma unroll
-            for (int k = 0; k < kG; ++k)
-                d[k] = pos[k] >= 0 ? (int)(keys[pos[k]] >> shift) & 0xff : kSortBins + lane;
-            // batches in segment order, so equal digits keep their order
-#pragma unroll
-            for (int k = 0; k < kG; ++k) {
-                if (b0 + 32 * k >= s1) break;
-                const bool valid = pos[k] >= 0;
-                const uint32_t peers = __match_any_sync(kFull, d[k]);
-                uint32_t base = 0;
-                if (valid) base = hw[d[k]];
-                __syncwarp();
-                if (valid) {
-                    dst[base + __popc(peers & lanemask_lt())] = (Pos)pos[k];
-                    if (lane == __ffs(peers) - 1) hw[d[k]] = base + __popc(peers);
+    // the stable passes, compiled for digits looked up in `dig` and for digits taken from the keys
+    auto stable_passes = [&](auto use_dig) {
+        constexpr bool kDig = decltype(use_dig)::value;
+        for (int pass = 0; pass < kPasses; ++pass) {
+            const int shift = kBits0 + 8 * pass;
+            if constexpr (kDig) {
+                const int nq = (area + 3) >> 2;  // keys of 4 consecutive box positions per load
+                const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+                uint32_t* d4 = reinterpret_cast<uint32_t*>(dig);
+                for (int j = tid; j < nq; j += nthreads) {
+                    const uint4 q = k4[j];
+                    d4[j] = ((q.x >> shift) & 0xffu) | (((q.y >> shift) & 0xffu) << 8) |
+                            (((q.z >> shift) & 0xffu) << 16) | ((q.w >> shift) << 24);
                 }
-                __syncwarp();
+                G.sync();
             }
+            auto digit = [&](int pos) -> int {
+                if constexpr (kDig) return dig[pos];
+                else return (int)(keys[pos] >> shift) & 0xff;
+            };
+            for (int d = lane; d < kSortBins; d += 32) hw[d] = 0;
+            __syncwarp();
+            for (int i0 = s0 + lane; i0 < s1; i0 += 32 * kG) {  // counts do not depend on the order
+                int dk[kG];
+#pragma unroll
+                for (int k = 0; k < kG; ++k) {
+                    const int i = i0 + 32 * k;
+                    dk[k] = i < s1 ? digit(src[i]) : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < kG; ++k)
+                    if (i0 + 32 * k < s1) atomicAdd(&hw[dk[k]], 1u);
+            }
+            G.sync();
+            scan_counts();
+            G.sync();
+            for (int b0 = s0; b0 < s1; b0 += 32 * kG) {
+                int pos[kG], d[kG];
+#pragma unroll
+                for (int k = 0; k < kG; ++k) {
+                    const int i = b0 + 32 * k + lane;
+                    pos[k] = i < s1 ? (int)src[i] : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < kG; ++k)
+                    d[k] = pos[k] >= 0 ? digit(pos[k]) : kSortBins + lane;
+                // batches in segment order, so equal digits keep their order
+#pragma unroll
+                for (int k = 0; k < kG; ++k) {
+                    if (b0 + 32 * k >= s1) break;
+                    const bool valid = pos[k] >= 0;
+                    const uint32_t peers = __match_any_sync(kFull, d[k]);
+                    uint32_t base = 0;
+                    if (valid) base = hw[d[k]];
+                    __syncwarp();
+                    if (valid) {
+                        dst[base + __popc(peers & lanemask_lt())] = (Pos)pos[k];
+                        if (lane == __ffs(peers) - 1) hw[d[k]] = base + __popc(peers);
+                    }
+                    __syncwarp();
+                }
+            }
+            G.sync();
+            src = dst;
+            dst = (dst == bufA) ? bufB : bufA;
         }
-        G.sync();
-        src = dst;
-        dst = (dst == bufA) ? bufB : bufA;
+    };
+    if constexpr (DT == FIM_F32) {  // only float plans place digits (one stable pass otherwise)
+        if (dig != nullptr)
+            stable_passes(std::true_type{});
+        else
+            stable_passes(std::false_type{});
+    } else {
+        stable_passes(std::false_type{});
     }
     // the sorted positions are in B; rewrite them in place as entries
     typename Loc<W>::E* om = reinterpret_cast<typename Loc<W>::E*>(bufB);
@@ -1234,19 +1264,21 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                                                          place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
                                                          place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
                                                          reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc,
-                                                         reinterpret_cast<uint32_t*>(smem + P.loc_bins), fp, G);
+                                                         reinterpret_cast<uint32_t*>(smem + P.loc_bins),
+                                                         P.loc_dig >= 0 ? smem + P.loc_dig : nullptr, fp, G);
             else
                 ordinal_transform_radix<DT, W, false, ST>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
                                                           place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
                                                           place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
                                                           reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc,
-                                                          nullptr, fp, G);
+                                                          nullptr, P.loc_dig >= 0 ? smem + P.loc_dig : nullptr, fp,
+                                                          G);
         } else if (DT == FIM_U16 && P.sort == kSortRadix) {
             ordinal_transform_radix<DT, W, false, ST>(P, frow, place<uint32_t>(smem, gslice, P.loc_keys),
                                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_a),
                                                       place<typename Loc<W>::Pos>(smem, gslice, P.loc_b),
                                                       reinterpret_cast<uint32_t*>(smem + P.loc_hist), misc, nullptr,
-                                                      fp, G);
+                                                      P.loc_dig >= 0 ? smem + P.loc_dig : nullptr, fp, G);
         } else {
             ordinal_transform_count<DT, W, ST>(P, frow, reinterpret_cast<uint32_t*>(smem + P.loc_bins), misc, om, fp,
                                                G);
