@@ -56,21 +56,28 @@ def parse():
     ap.add_argument("--no-sections", action="store_true",
                     help="skip the radius sweep and the 8-bit and float workloads")
     ap.add_argument("--train-images", type=int, default=200)
-    ap.add_argument("--profile-case", default=None, metavar="SIDE:R",
-                    help="only run two launches on a SIDE x SIDE crop of the image at radius R (for ncu)")
+    ap.add_argument("--profile-case", default=None, metavar="[f32:]SIDE:R",
+                    help="only run two launches on a SIDE x SIDE crop of the image at radius R (for ncu); "
+                         "f32: the float field instead of the 16-bit image")
     return ap.parse_args()
 
 
 def run_profile_case(spec: str) -> int:
-    """Two launches of the tile kernel on a small crop: the case the ncu captures use."""
+    """Two launches of the tile kernel on a small crop: the case the ncu captures use.
+    SIDE:R is the 16-bit photo-like image; f32:SIDE:R the float field."""
     import numpy as np
     import torch
 
     import datagen
     import paper_2505_22938_gb300 as fim
-    side, r = (int(v) for v in spec.split(":"))
-    img = datagen.config2_image(side, side)
-    src = torch.from_numpy(img.view(np.int16)).cuda().view(torch.uint16)
+    parts = spec.split(":")
+    f32 = parts[0] == "f32"
+    side, r = (int(v) for v in parts[-2:])
+    if f32:
+        src = datagen.torch_field_f32(datagen.seed_for(3, 0), side, side)
+    else:
+        img = datagen.config2_image(side, side)
+        src = torch.from_numpy(img.view(np.int16)).cuda().view(torch.uint16)
     out = torch.empty_like(src)
     k = fim.fim_create_kernel_circle(r)
     for _ in range(2):
