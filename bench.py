@@ -385,6 +385,36 @@ def config3_section(fim, torch, flush, clock_mhz, reps: int = 3):
             "status": fim.fim_sync_status(sh)}
 
 
+def u8_section(fim, torch, flush, clock_mhz, reps: int = 5):
+    """u8 4096x4096 uniform noise (the 8-bit workload at a size that fills the GPU), disk r = 4,
+    16 and 48: Mpix/s and roofline fraction, two whole rows each checked against the oracle."""
+    import datagen
+    import oracle
+    n = 4096
+    img = datagen.torch_uniform_u8(datagen.seed_for(1, 1), n, n)
+    host = img.cpu().numpy()
+    out = torch.empty_like(img)
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    res, px_all, bad_all = {}, 0, 0
+    for r in (4, 16, 48):
+        k = fim.fim_create_kernel_circle(r)
+
+        def run():
+            fim.fim_median(img.data_ptr(), out.data_ptr(), n, n, n, fim.FIM_U8, k, sh)
+
+        run()
+        ms = timed_launch_ms(torch, run, reps, flush)
+        e = roofline_entry(fim, k, fim.FIM_U8, "u8", n, n, ms, r, None, clock_mhz)
+        px, bad = band_parity(host, out, oracle.disk_offsets(r), (0, n // 2 + 5))
+        e["parity_pixels"], e["parity_mismatches"] = px, bad
+        px_all += px
+        bad_all += bad
+        res[f"r{r}"] = e
+    del img, out
+    return {"workload": "u8 4096x4096 uniform, disk r = 4,16,48", "per_radius": res,
+            "parity": {"pixels": px_all, "mismatches": bad_all}, "status": fim.fim_sync_status(sh)}
+
+
 def config1_section(fim, torch, reps: int = 20):
     """u8 256x256 uniform noise, disk r = 4: the whole output against the oracle; the time is
     the mean of back-to-back calls (a launch-bound size)."""
@@ -908,8 +938,9 @@ def run_native(args):
         line["config1"] = config1_section(fim, torch)
         line["sweep_u16"] = sweep_section(fim, torch, src, img, flush, clock_for_peak)
         line["config3"] = config3_section(fim, torch, flush, clock_for_peak)
+        line["u8_4096"] = u8_section(fim, torch, flush, clock_for_peak)
         line["sections_clocks"] = sec_clocks.stop()
-        for name in ("config1", "sweep_u16", "config3"):
+        for name in ("config1", "sweep_u16", "config3", "u8_4096"):
             if line[name]["parity"]["mismatches"] or line[name]["status"]:
                 failed.append(name)
     if world == 1 and not args.no_batched:

@@ -232,7 +232,7 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     while ((1 << p->txshift) < ts.Tx) ++p->txshift;
     if ((1 << p->txshift) != ts.Tx || ts.Tx % 32 != 0 || ts.Ty % ts.RB != 0 || ts.Tx % ts.G != 0 ||
         ts.Ty / ts.RB < 1 || ts.Tx / ts.G < 2)
-        return FIM_ERR_INTERNAL;
+        return FIM_ERR_UNSUPPORTED;
     p->RB = ts.RB;
     p->G = ts.G;
     p->vthreads = 2 * ts.Tx * ts.RB;
@@ -241,7 +241,7 @@ fim_status make_plan(const fim_kernel* k, int dtype, int rank, int w, int h, con
     // large tiles (8): measured on the 4096^2 photo-like workload, each within 2 % of the best.
     p->scan_groups = p->vthreads < 1024 ? 4 : 8;
     p->nwarps = p->threads / 32;
-    if (p->threads > 1024 || p->threads % 32 != 0) return FIM_ERR_INTERNAL;
+    if (p->threads > 1024 || p->threads % 32 != 0) return FIM_ERR_UNSUPPORTED;  // 2 x Tx x bands threads
     p->shape = k->shape;
     p->r2 = (int)k->r2;
     p->xmin = k->xmin;
@@ -541,33 +541,59 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     // beyond: taller 64x128 tiles, which halve the seed and seed-row work per pixel.
     const int extent = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1;
     const int first = extent <= 33 ? 0 : (extent <= 45 ? 1 : (extent >= 65 ? 2 : 3));
-    // A footprint beyond 65535 pixels (ranks relative to the feasible range) sorts by radix passes
-    // on global lists; an exact-rank plan keeps its sort in shared memory. The first exact-rank
-    // shape wins unless its tile is tiny (under 2048 pixels, where the per-pixel sort work
-    // explodes); then the first larger-footprint shape seen before it does (measured, 4096^2
-    // u16: r = 96 2.98 Gpix/s on 64x64 against 2.13 on 64x128; r = 128 1.04 on 64x64 against
-    // 0.21 on 32x16).
-    const TileShape* wide_choice = nullptr;
-    for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
-        const TileShape& c = cands[i];
+    // Beyond the first valid shape, two measured exceptions (4096^2 photo-like u16, 4096^2 u8,
+    // 8192^2 f32):
+    // (1) where its omnigram spills to global scratch, a later shape of at least 64x64 whose
+    //     omnigram stays in shared memory wins (u16 r = 80: 5.04 Gpix/s on 64x64 against 3.37
+    //     on 64x128);
+    // (2) for 16-bit data, whose footprints beyond 65535 pixels (ranks relative to the feasible
+    //     range) count in two rounds and seed by walks, the first exact-rank shape wins unless
+    //     its tile is under 2048 pixels (r = 96: 3.01 on 64x64 against 2.82 on 64x128). 8-bit
+    //     data (256 bins) and float keys (radix passes on global lists at these sizes) keep the
+    //     larger tile (u8 r = 96: 4.30 on 64x128 against 3.43; f32 r = 100: 1.75 against 1.67).
+    struct Info {
+        bool ok;
+        int n;
+        bool om_smem;
+    };
+    auto probe = [&](const TileShape& c, Info* inf) {
+        inf->ok = false;
         Plan* p = new (std::nothrow) Plan;
         if (!p) return FIM_ERR_OOM;
-        fim_status s = make_plan(k, dtype, 0, 1, 1, c, smem_limit, p, cta_threads, exact_ranks);
-        const int bytes = p->smem_bytes, n = p->N;
+        const fim_status s = make_plan(k, dtype, 0, 1, 1, c, smem_limit, p, cta_threads, exact_ranks);
+        inf->ok = s == FIM_OK && p->smem_bytes <= smem_limit;
+        inf->n = p->N;
+        inf->om_smem = p->loc_om >= 0;
         delete p;
-        if (s != FIM_OK || bytes > smem_limit) continue;
-        if (n > 65535) {
-            if (!wide_choice) wide_choice = &c;
-            continue;
+        return FIM_OK;
+    };
+    const int ncands = (int)(sizeof(cands) / sizeof(cands[0]));
+    int i0 = -1;
+    Info f{};
+    for (int i = first; i < ncands && i0 < 0; ++i) {
+        if (probe(cands[i], &f) != FIM_OK) return FIM_ERR_OOM;
+        if (f.ok) i0 = i;
+    }
+    if (i0 < 0) return FIM_ERR_UNSUPPORTED;
+    Info g{};
+    if (!f.om_smem)
+        for (int i = i0 + 1; i < ncands; ++i) {
+            if (probe(cands[i], &g) != FIM_OK) return FIM_ERR_OOM;
+            if (g.ok && g.om_smem && cands[i].Tx * cands[i].Ty >= 4096) {
+                *ts = cands[i];
+                return FIM_OK;
+            }
         }
-        *ts = wide_choice && c.Tx * c.Ty < 2048 ? *wide_choice : c;
-        return FIM_OK;
-    }
-    if (wide_choice) {
-        *ts = *wide_choice;
-        return FIM_OK;
-    }
-    return FIM_ERR_UNSUPPORTED;
+    if (dtype == FIM_U16 && f.n > 65535)
+        for (int i = i0 + 1; i < ncands; ++i) {
+            if (probe(cands[i], &g) != FIM_OK) return FIM_ERR_OOM;
+            if (g.ok && g.n <= 65535) {
+                *ts = cands[i].Tx * cands[i].Ty < 2048 ? cands[i0] : cands[i];
+                return FIM_OK;
+            }
+        }
+    *ts = cands[i0];
+    return FIM_OK;
 }
 
 }  // namespace fim

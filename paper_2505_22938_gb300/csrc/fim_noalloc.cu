@@ -44,23 +44,44 @@ fim_status workspace_address(unsigned char** out) {
     return FIM_OK;
 }
 
-// The library's default tile shapes, in its order of preference by kernel extent (small kernels:
-// 32x32 tiles in small CTAs first), without the autotuner's cache, whose lookup allocates. A
-// candidate is taken when it fits shared memory and its launch fits the fixed array (per-CTA
-// buffers of large kernels times the resident CTAs); the plan is built in the caller's storage.
+// The library's default tile choice (its shapes in its order of preference by kernel extent,
+// small kernels on 32x32 tiles in small CTAs first, and its two exceptions past the first valid
+// shape: a later shape of at least 64x64 that keeps the omnigram in shared memory where the
+// first one spills it, and for 16-bit data the first exact-rank shape), without the autotuner's
+// cache, whose lookup allocates. A candidate is valid when it fits shared memory and its launch
+// fits the fixed array (per-CTA buffers of large kernels times the resident CTAs). Trial plans
+// and the chosen one are built in the caller's storage.
 fim_status pick_plan(const fim_kernel* k, int dtype, int w, int h, int limit, fim::Plan* plan) {
     static const fim::TileShape cands[] = {{32, 32, 2, 1}, {32, 32, 4, 1}, {64, 128, 8, 2}, {64, 64, 8, 2},
                                            {32, 64, 8, 2}, {32, 32, 8, 2}, {32, 16, 8, 2}};
+    const int ncands = (int)(sizeof(cands) / sizeof(cands[0]));
     const int extent = (k->xmax - k->xmin > k->ymax - k->ymin ? k->xmax - k->xmin : k->ymax - k->ymin) + 1;
     const int first = extent <= 33 ? 0 : (extent <= 45 ? 1 : (extent >= 65 ? 2 : 3));
-    for (int i = first; i < (int)(sizeof(cands) / sizeof(cands[0])); ++i) {
-        if (fim::make_plan(k, dtype, (k->n - 1) / 2, w, h, cands[i], limit, plan) != FIM_OK ||
-            plan->smem_bytes > limit)
-            continue;
-        if (fim::launch_tile_kernel_fixed(*plan, nullptr, FIM_NOALLOC_WORKSPACE_BYTES, nullptr, false) == FIM_OK)
-            return FIM_OK;
-    }
-    return FIM_ERR_UNSUPPORTED;
+    auto valid = [&](int i) {
+        return fim::make_plan(k, dtype, (k->n - 1) / 2, w, h, cands[i], limit, plan) == FIM_OK &&
+               plan->smem_bytes <= limit &&
+               fim::launch_tile_kernel_fixed(*plan, nullptr, FIM_NOALLOC_WORKSPACE_BYTES, nullptr, false) == FIM_OK;
+    };
+    int i0 = -1;
+    for (int i = first; i < ncands && i0 < 0; ++i)
+        if (valid(i)) i0 = i;
+    if (i0 < 0) return FIM_ERR_UNSUPPORTED;
+    const bool om_smem = plan->loc_om >= 0;
+    const int n0 = plan->N;
+    int pick = i0;
+    if (!om_smem)
+        for (int i = i0 + 1; i < ncands; ++i)
+            if (valid(i) && plan->loc_om >= 0 && cands[i].Tx * cands[i].Ty >= 4096) {
+                pick = i;
+                break;
+            }
+    if (pick == i0 && dtype == FIM_U16 && n0 > 65535)
+        for (int i = i0 + 1; i < ncands; ++i)
+            if (valid(i) && plan->N <= 65535) {
+                pick = cands[i].Tx * cands[i].Ty < 2048 ? i0 : i;
+                break;
+            }
+    return valid(pick) ? FIM_OK : FIM_ERR_UNSUPPORTED;
 }
 
 bool overlap(const void* a, const void* b, size_t bytes) {

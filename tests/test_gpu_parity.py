@@ -165,9 +165,11 @@ def test_full_size_config2_sampled():
 
 
 @pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
-@pytest.mark.parametrize("r", [100, 113, 128])
+@pytest.mark.parametrize("r", [80, 96, 100, 113, 128])
 def test_large_radius(dtype, r):
-    """Kernels whose footprint needs global scratch (radix keys, 32-bit omnigram entries)."""
+    """Kernels whose footprint needs global scratch (radix keys, 32-bit omnigram entries), or
+    whose default tile is the smaller one that keeps the omnigram in shared memory (r = 80), or
+    whose footprints exceed 65535 pixels on the larger tile (8-bit and float data keep it)."""
     img = datagen.image_for(dtype, 500 + r, 45, 71)
     run_case(img, "circle", r)
 
