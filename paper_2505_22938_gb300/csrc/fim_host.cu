@@ -548,7 +548,8 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     //     on 64x128);
     // (2) for 16-bit data, whose footprints beyond 65535 pixels (ranks relative to the feasible
     //     range) count in two rounds and seed by walks, the first exact-rank shape wins unless
-    //     its tile is under 2048 pixels (r = 96: 3.01 on 64x64 against 2.82 on 64x128). 8-bit
+    //     its tile is under 64x64 (r = 96: 3.01 on 64x64 against 2.82 on 64x128; r = 112: 2.31
+    //     on 64x128 against 0.88 on the exact-rank 32x64). 8-bit
     //     data (256 bins) and float keys (radix passes on global lists at these sizes) keep the
     //     larger tile (u8 r = 96: 4.30 on 64x128 against 3.43; f32 r = 100: 1.75 against 1.67).
     struct Info {
@@ -588,7 +589,7 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
         for (int i = i0 + 1; i < ncands; ++i) {
             if (probe(cands[i], &g) != FIM_OK) return FIM_ERR_OOM;
             if (g.ok && g.n <= 65535) {
-                *ts = cands[i].Tx * cands[i].Ty < 2048 ? cands[i0] : cands[i];
+                *ts = cands[i].Tx * cands[i].Ty < 4096 ? cands[i0] : cands[i];
                 return FIM_OK;
             }
         }

@@ -47,8 +47,8 @@ fim_status workspace_address(unsigned char** out) {
 // The library's default tile choice (its shapes in its order of preference by kernel extent,
 // small kernels on 32x32 tiles in small CTAs first, and its two exceptions past the first valid
 // shape: a later shape of at least 64x64 that keeps the omnigram in shared memory where the
-// first one spills it, and for 16-bit data the first exact-rank shape), without the autotuner's
-// cache, whose lookup allocates. A candidate is valid when it fits shared memory and its launch
+// first one spills it, and for 16-bit data the first exact-rank shape of at least 64x64),
+// without the autotuner's cache, whose lookup allocates. A candidate is valid when it fits shared memory and its launch
 // fits the fixed array (per-CTA buffers of large kernels times the resident CTAs). Trial plans
 // and the chosen one are built in the caller's storage.
 fim_status pick_plan(const fim_kernel* k, int dtype, int w, int h, int limit, fim::Plan* plan) {
@@ -78,7 +78,7 @@ fim_status pick_plan(const fim_kernel* k, int dtype, int w, int h, int limit, fi
     if (pick == i0 && dtype == FIM_U16 && n0 > 65535)
         for (int i = i0 + 1; i < ncands; ++i)
             if (valid(i) && plan->N <= 65535) {
-                pick = cands[i].Tx * cands[i].Ty < 2048 ? i0 : i;
+                pick = cands[i].Tx * cands[i].Ty < 4096 ? i0 : i;
                 break;
             }
     return valid(pick) ? FIM_OK : FIM_ERR_UNSUPPORTED;
