@@ -155,7 +155,7 @@ struct Plan {
     int htab[2 * kMaxExtent];             // per row i: dy*SP + lo, dy*SP + hi + 1
     int spans[kMaxExtent];                // per row i: (lo & 0xffff) | (hi << 16)
     // tensor map of the input image for the footprint copies (valid when use_tma)
-    alignas(64) CUtensorMap tmap;
+    CUtensorMap tmap;  // (the type carries the alignment the copies need)
 };
 
 // Bytes of a Plan before its tables: all the tile pipeline reads once the tables are in
