@@ -29,6 +29,12 @@ struct fim_batch {
     unsigned char* scratch = nullptr;         // per class, grid * scratch_per_cta bytes
     std::vector<cudaStream_t> side;           // classes after the first run on these
     std::vector<cudaEvent_t> ev;              // fork event, then one join event per side stream
+    // per class (launch order): a one-job class runs the single-image kernel on its plan (kept
+    // here) over the class's workspace, whose first 256 bytes then hold that kernel's queue
+    std::vector<char> solo;
+    std::vector<Plan> solo_plan;
+    std::vector<unsigned char*> cls_scratch;
+    std::vector<size_t> cls_bytes;
     int device = 0;
 };
 
@@ -124,6 +130,7 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
         p.out = j.out;
         p.pitch = (long long)j.pitch_bytes;
         p.ntiles = p.tiles_x * p.tiles_y;
+        attach_tma(p);  // the class kernels stage interior footprints like the single-image kernel
     }
     // classes: the instantiation a plan runs on and its CTA size
     auto key = [&](const Plan& p) {
@@ -186,7 +193,7 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
         }
         k.grid = (int)std::min<long long>(k.total_tiles, (long long)occ * device_sm_count());
         scratch_off[c] = scratch_bytes;
-        scratch_bytes += ((size_t)k.grid * (size_t)k.scratch_per_cta + 255) & ~(size_t)255;
+        scratch_bytes += 256 + (((size_t)k.grid * (size_t)k.scratch_per_cta + 255) & ~(size_t)255);
     }
     if (cudaMalloc(&b->d_plans, sizeof(Plan) * (size_t)count) != cudaSuccess ||
         cudaMalloc(&b->d_tile_start, sizeof(int) * (size_t)count) != cudaSuccess ||
@@ -215,10 +222,20 @@ fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out) {
         a.total_tiles = k.total_tiles;
         a.counter = reinterpret_cast<unsigned int*>(reinterpret_cast<unsigned char*>(b->d_counters) +
                                                     256 * b->classes.size());
-        a.scratch = b->scratch ? b->scratch + scratch_off[c] : nullptr;
+        a.scratch = b->scratch ? b->scratch + scratch_off[c] + 256 : nullptr;
         a.scratch_per_cta = k.scratch_per_cta;
         b->classes.push_back(k);
         b->args.push_back(a);
+        // A class of one job runs the single-image kernel (its plan as the kernel parameter, no
+        // job lookup), where that kernel's grid fits the class's workspace.
+        const size_t bytes = 256 + (((size_t)k.grid * (size_t)k.scratch_per_cta + 255) & ~(size_t)255);
+        Plan solo = sorted[first_job[c]];
+        const bool one = k.njobs == 1 && b->scratch != nullptr &&
+                         launch_tile_kernel_fixed(solo, nullptr, bytes, nullptr, false) == FIM_OK;
+        b->solo.push_back(one ? 1 : 0);
+        b->solo_plan.push_back(solo);
+        b->cls_scratch.push_back(b->scratch ? b->scratch + scratch_off[c] : nullptr);
+        b->cls_bytes.push_back(bytes);
     }
     for (int c = 1; c < ncls; ++c) {
         cudaStream_t st;
@@ -251,7 +268,13 @@ fim_status fim_batch_run(fim_batch* b, void* stream) {
     for (int c = 0; c < ncls; ++c) {
         cudaStream_t cs = c == 0 ? st : b->side[c - 1];
         if (c > 0 && cudaStreamWaitEvent(cs, b->ev[0], 0) != cudaSuccess) return FIM_ERR_CUDA;
-        fim_status s = class_kernel(b->classes[c], &b->args[c], nullptr, cs);
+        fim_status s;
+        if (b->solo[c]) {
+            Plan p = b->solo_plan[c];
+            s = launch_tile_kernel_fixed(p, b->cls_scratch[c], b->cls_bytes[c], cs, true);
+        } else {
+            s = class_kernel(b->classes[c], &b->args[c], nullptr, cs);
+        }
         if (s != FIM_OK) return s;
         if (c > 0 && cudaEventRecord(b->ev[c], cs) != cudaSuccess) return FIM_ERR_CUDA;
     }

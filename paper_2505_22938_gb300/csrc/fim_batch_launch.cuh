@@ -31,9 +31,14 @@ __global__ void __launch_bounds__(1024, 1) batch_class_kernel(const __grid_const
     // the current job's plan scalars (everything before the tables); the tables go to the
     // dynamic shared memory as in the single-image kernel
     __shared__ __align__(16) unsigned char s_plan[kPlanScalarBytes];
+    // the footprint copies' mbarrier, one for the CTA's whole run (the jobs' tensor maps stay in
+    // the plan array in global memory)
+    __shared__ __align__(8) uint64_t s_bar;
     const int tid = threadIdx.x;
     unsigned char* gslice = A.scratch + (size_t)blockIdx.x * (size_t)A.scratch_per_cta;
     const Grp G{tid, tid & 31, tid >> 5, (int)blockDim.x, 0, 0};
+    TmaState tma{0u, 0};
+    if (tid == 0) mbar_init(&s_bar);  // visible after the loop's first barrier
     int cur = -1;
     for (;;) {
         if (tid == 0) {
@@ -54,7 +59,8 @@ __global__ void __launch_bounds__(1024, 1) batch_class_kernel(const __grid_const
             cur = job;
         }
         const Plan& P = *reinterpret_cast<const Plan*>(s_plan);
-        process_tile<DT, SHAPE, W, OG, KS, 0, false>(P, t - __ldg(A.tile_start + job), gslice, G);
+        process_tile<DT, SHAPE, W, OG, KS, 0, 2>(P, t - __ldg(A.tile_start + job), gslice, G, &tma, &s_bar,
+                                                 &A.plans[job].tmap);
     }
 }
 

@@ -19,11 +19,9 @@ __global__ void __launch_bounds__(1024, 1) tile_median_kernel(const __grid_const
     unsigned int* counter = reinterpret_cast<unsigned int*>(P.scratch);
     const Grp G{tid, tid & 31, tid >> 5, (int)blockDim.x, 0, 0};
     // the footprint copies' mbarrier (scan scratch words 34-35), initialised before the first tile
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     TmaState tma{0u, 0};
-    if (P.use_tma && tid == 0) {
-        extern __shared__ __align__(16) unsigned char smem_dyn[];
-        mbar_init(reinterpret_cast<uint64_t*>(smem_dyn + P.off_misc + 34 * 4));
-    }
+    if (P.use_tma && tid == 0) mbar_init(reinterpret_cast<uint64_t*>(smem_dyn + P.off_misc + 34 * 4));
     for (;;) {
         if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
         __syncthreads();

@@ -381,7 +381,7 @@ constexpr int kHandoff = 8;
 constexpr int kHandoffAfterGroups = 8;
 
 // KS > 0: KS groups per step, fixed at compile time; KS = 0: `groups` per step (at most 8),
-// read at run time (smaller code, for the batch kernel that serves every plan).
+// read at run time (smaller code).
 template <int SHAPE, int W, int KS>
 __device__ __forceinline__ int thread_select(const typename Loc<W>::E* __restrict__ om, int N, int p, int c,
                                              int target, int px, int py, const Member<SHAPE, W>& member,
@@ -1181,18 +1181,20 @@ __device__ int compact_omnigram(typename Loc<W>::E* om, int N, const int* qfrow,
     return base;
 }
 
-// KS: omnigram groups per scan step of the vertical sweep, fixed at compile time (4 or 8), or
-// 0 to follow the plan's scan_groups at run time (the batch kernel, which serves every plan:
-// one run-time loop keeps its 18 inlined pipelines small enough to compile quickly).
+// KS: omnigram groups per scan step of the vertical sweep, fixed at compile time (4 or 8; the
+// batch class kernels are compiled for both), or 0 to follow the plan's scan_groups at run time.
 // XT: 1 compiles the extras — the learned bracket, training-row output, seed statistics and
 // several target ranks per launch — and 2 a target rank per output pixel (a percentile map).
 // Each lives in kernels of its own: at the 64-register cap of 1024-thread CTAs their code
 // changes how the compiler allocates the plain pipeline's registers, and the reverse.
-// TMA: the footprint copies are compiled in (the single-image kernels, whose plan is a kernel
-// parameter the copies can name; the batch kernels read their plans from shared memory).
-template <int DT, int SHAPE, int W, int OG, int KS = 0, int XT = 0, bool TMA = true>
+// TMA: how interior footprints are copied into the staging region: 0 not at all; 1 the
+// single-image kernels (mbarrier in the scan scratch, tensor map in the kernel parameter);
+// 2 the batch kernels (`bar` and `tmap` given: a CTA-wide mbarrier and the job's tensor map in
+// the plan array in global memory, since their plans are read from shared memory).
+template <int DT, int SHAPE, int W, int OG, int KS = 0, int XT = 0, int TMA = 1>
 __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned char* gslice, const Grp& G,
-                                             TmaState* tma = nullptr) {
+                                             TmaState* tma = nullptr, uint64_t* bar = nullptr,
+                                             const void* tmap = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_base[];
     unsigned char* const smem = smem_base + G.shift;  // this group's partition (tables excluded)
     using V = typename Traits<DT>::T;
@@ -1232,15 +1234,18 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
     // into shared memory, and every thread waits on the mbarrier (bounded: after a timeout the
     // tile, and the CTA's later tiles, read the image instead).
     Footprint<DT> fp{nullptr, 0, 0, Img(P), gx0, gy0};
-    if (TMA && tma != nullptr && P.use_tma && !tma->off) {
+    if (TMA != 0 && tma != nullptr && P.use_tma && !tma->off) {
         constexpr int A = 16 / (int)sizeof(V);  // elements per 16 bytes
         const int x0 = gx0 & ~(A - 1);
         if (x0 >= 0 && gy0 >= 0 && x0 + P.stage_bw <= P.w && gy0 + P.SH <= P.h) {
             unsigned char* st = smem + P.loc_stage;
             st += (128u - (smem_addr(st) & 127u)) & 127u;  // the region has 128 bytes of slack
-            uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 34);
+            if constexpr (TMA == 1) {  // the single-image kernel: barrier in the scan scratch
+                bar = reinterpret_cast<uint64_t*>(misc + 34);
+                tmap = &P.tmap;
+            }
             if (tid == 0)
-                tma_load_box(&P.tmap, st, bar, x0, gy0, (uint32_t)(P.stage_bw * P.SH * (int)sizeof(V)));
+                tma_load_box(tmap, st, bar, x0, gy0, (uint32_t)(P.stage_bw * P.SH * (int)sizeof(V)));
             const bool ok = mbar_wait(bar, tma->parity) || mbar_wait(bar, tma->parity);
             tma->parity ^= 1u;
             if (ok) {
@@ -1284,7 +1289,7 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                                                G);
         }
     };
-    if constexpr (TMA) {
+    if constexpr (TMA != 0) {
         if (fp.stage != nullptr)
             sort(std::true_type{});
         else

@@ -134,3 +134,33 @@ def test_autotune_then_filter():
         assert_bit_exact(to_host(out), exp, "autotune output")
     finally:
         fim.fim_autotune_clear()
+
+
+@pytest.mark.parametrize("dtype,r", [("u8", 16), ("u16", 48), ("f32", 64)])
+def test_one_job_batch_and_two_job_class(dtype, r):
+    """A class of one job runs the single-image kernel over the class's workspace; two jobs of
+    the same class run the class kernel. Both match fim_median byte for byte and the oracle on
+    sampled pixels (images wide enough for interior tiles, whose footprints the kernels stage)."""
+    import torch
+    import paper_2505_22938_gb300 as fim
+    img = datagen.image_for(dtype, 700 + r, 300, 260)
+    store, view = to_device(img, pitch_elems=272)  # rows of a multiple of 16 bytes: staged copies
+    k = fim.fim_create_kernel_circle(r)
+    ref = fim.median(view, k, out=torch.empty_like(store)[:, :260])
+    torch.cuda.synchronize()
+    code = {"u8": fim.FIM_U8, "u16": fim.FIM_U16, "f32": fim.FIM_F32}[dtype]
+    pitch = store.stride(0) * store.element_size()
+    for njobs in (1, 2):
+        outs = [torch.empty_like(store) for _ in range(njobs)]
+        jobs = [fim.make_job(store.data_ptr(), o.data_ptr(), 260, 300, pitch, code, k) for o in outs]
+        batch = fim.fim_batch_create(jobs, [k])
+        batch.run(torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert fim.fim_sync_status() == 0
+        for o in outs:
+            assert_bit_exact(to_host(o[:, :260]), to_host(ref), f"{njobs}-job batch vs fim_median")
+    rng = np.random.default_rng(r)
+    ys, xs = rng.integers(0, 300, 200), rng.integers(0, 260, 200)
+    exp = oracle.median_points(img, oracle.disk_offsets(r), xs.astype(np.int32), ys.astype(np.int32))
+    got = to_host(ref)[ys, xs]
+    assert np.array_equal(got.view(np.uint8), np.ascontiguousarray(exp).view(np.uint8))
