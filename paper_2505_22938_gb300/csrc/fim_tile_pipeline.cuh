@@ -1595,9 +1595,10 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
                 const uint16_t* ctr = ord + cv * SP + cu + eoff;
                 const int pr = p - rb;  // the pivot among the ordinal image's ranks
                 int d = 0;
-                // slide unrolled 8 kernel columns deep in the 1024-thread kernels, 4 in the small
-                // CTAs (measured, 4096^2 u16: r = 32-64 +1.2-1.8 % over 4; r = 2-16 -3 to -11 %)
-                constexpr int kSlideUnroll = KS == 4 ? 4 : 8;
+                // slide unrolled 8 kernel columns deep in the kernels compiled for the 1024-thread
+                // tiles (KS = 8), 4 in the others (measured, 4096^2 u16: r = 32-64 +1.2-1.8 % over
+                // 4; r = 2-16 -3 to -11 %; KS = 0 kernels serve small CTAs too)
+                constexpr int kSlideUnroll = KS == 8 ? 8 : 4;
                 if (down) {
     #pragma unroll kSlideUnroll
                     for (int j = 0; j < ncols; ++j) {
