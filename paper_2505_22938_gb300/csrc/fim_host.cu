@@ -496,6 +496,37 @@ fim_status layout_plan(Plan* p, int smem_limit, bool stage_model) {
     return FIM_OK;
 }
 
+// CTAs of a plan resident per SM: its threads at 64 registers each (the kernels' cap), its
+// shared memory plus the 1 KiB the runtime reserves per CTA.
+static int resident_ctas(const Plan& p) {
+    const int per_sm = device_smem_per_sm();
+    const int by_regs = 65536 / (p.threads * 64);
+    const int by_smem = per_sm > 0 ? per_sm / (p.smem_bytes + 1024) : 1;
+    return std::max(1, std::min(std::min(by_regs, by_smem), std::min(2048 / p.threads, 32)));
+}
+
+bool small_image_shape(const fim_kernel* k, int dtype, int w, int h, int smem_limit, int cta_threads,
+                       bool exact_ranks, const TileShape& def, Plan* scratch, TileShape* out) {
+    if ((long long)w * h <= 0) return false;
+    const int extent = std::max(k->xmax - k->xmin, k->ymax - k->ymin) + 1;
+    if (extent > 65) return false;
+    const int sms = device_sm_count();
+    auto tiles = [&](const TileShape& c) { return (long long)((w + c.Tx - 1) / c.Tx) * ((h + c.Ty - 1) / c.Ty); };
+    if (make_plan(k, dtype, 0, 1, 1, def, smem_limit, scratch, cta_threads, exact_ranks) != FIM_OK) return false;
+    if (2 * tiles(def) >= (long long)sms * resident_ctas(*scratch)) return false;
+    static const TileShape small[] = {{32, 8, 4, 1}, {32, 16, 4, 1}, {32, 8, 2, 1}};
+    for (const TileShape& c : small) {
+        if (make_plan(k, dtype, 0, 1, 1, c, smem_limit, scratch, cta_threads, exact_ranks) != FIM_OK ||
+            scratch->smem_bytes > smem_limit)
+            continue;
+        if (tiles(c) <= (long long)sms * resident_ctas(*scratch)) {
+            *out = c;
+            return true;
+        }
+    }
+    return false;
+}
+
 static bool parse_tile_env(TileShape* ts) {
     const char* e = getenv("FIM_TILE");
     if (!e || !*e) return false;
@@ -577,23 +608,30 @@ fim_status choose_tile(const fim_kernel* k, int dtype, int smem_limit, TileShape
     }
     if (i0 < 0) return FIM_ERR_UNSUPPORTED;
     Info g{};
+    int pick = i0;
     if (!f.om_smem)
-        for (int i = i0 + 1; i < ncands; ++i) {
+        for (int i = i0 + 1; i < ncands && pick == i0; ++i) {
             if (probe(cands[i], &g) != FIM_OK) return FIM_ERR_OOM;
-            if (g.ok && g.om_smem && cands[i].Tx * cands[i].Ty >= 4096) {
-                *ts = cands[i];
-                return FIM_OK;
-            }
+            if (g.ok && g.om_smem && cands[i].Tx * cands[i].Ty >= 4096) pick = i;
         }
-    if (dtype == FIM_U16 && f.n > 65535)
+    if (pick == i0 && dtype == FIM_U16 && f.n > 65535)
         for (int i = i0 + 1; i < ncands; ++i) {
             if (probe(cands[i], &g) != FIM_OK) return FIM_ERR_OOM;
             if (g.ok && g.n <= 65535) {
-                *ts = cands[i].Tx * cands[i].Ty < 4096 ? cands[i0] : cands[i];
-                return FIM_OK;
+                if (cands[i].Tx * cands[i].Ty >= 4096) pick = i;
+                break;
             }
         }
-    *ts = cands[i0];
+    *ts = cands[pick];
+    // Small images, whose tiles would fill under half the GPU's resident CTAs: the first of the
+    // smaller shapes that fits them all in one wave (measured, u8 256^2 r = 4 / 16 / 32: 58 /
+    // 50 / 134 us per call on the default tiles against 23 / 26 / 33 on 32x8 tiles with 4 bands;
+    // 512^2: 63 / 63 / 160 against 36 / 40 / 54 on 32x16; at 1024^2 the defaults stay ahead).
+    Plan* p = new (std::nothrow) Plan;
+    if (!p) return FIM_ERR_OOM;
+    TileShape small;
+    if (small_image_shape(k, dtype, w, h, smem_limit, cta_threads, exact_ranks, *ts, p, &small)) *ts = small;
+    delete p;
     return FIM_OK;
 }
 

@@ -47,8 +47,8 @@ fim_status workspace_address(unsigned char** out) {
 // The library's default tile choice (its shapes in its order of preference by kernel extent,
 // small kernels on 32x32 tiles in small CTAs first, and its two exceptions past the first valid
 // shape: a later shape of at least 64x64 that keeps the omnigram in shared memory where the
-// first one spills it, and for 16-bit data the first exact-rank shape of at least 64x64),
-// without the autotuner's cache, whose lookup allocates. A candidate is valid when it fits shared memory and its launch
+// first one spills it, and for 16-bit data the first exact-rank shape of at least 64x64; then
+// the smaller shapes of small images), without the autotuner's cache, whose lookup allocates. A candidate is valid when it fits shared memory and its launch
 // fits the fixed array (per-CTA buffers of large kernels times the resident CTAs). Trial plans
 // and the chosen one are built in the caller's storage.
 fim_status pick_plan(const fim_kernel* k, int dtype, int w, int h, int limit, fim::Plan* plan) {
@@ -81,6 +81,11 @@ fim_status pick_plan(const fim_kernel* k, int dtype, int w, int h, int limit, fi
                 pick = cands[i].Tx * cands[i].Ty < 4096 ? i0 : i;
                 break;
             }
+    fim::TileShape small;  // and the library's small-image rule, where its shape also fits the array
+    if (fim::small_image_shape(k, dtype, w, h, limit, 0, false, cands[pick], plan, &small) &&
+        fim::make_plan(k, dtype, (k->n - 1) / 2, w, h, small, limit, plan) == FIM_OK && plan->smem_bytes <= limit &&
+        fim::launch_tile_kernel_fixed(*plan, nullptr, FIM_NOALLOC_WORKSPACE_BYTES, nullptr, false) == FIM_OK)
+        return FIM_OK;
     return valid(pick) ? FIM_OK : FIM_ERR_UNSUPPORTED;
 }
 

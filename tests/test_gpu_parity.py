@@ -218,3 +218,37 @@ def test_full_size_config3_sampled():
         exp = oracle.median_points(img, oracle_offsets(*spec), xs, ys)
         assert np.array_equal(got.view(np.uint32), exp.view(np.uint32)), \
             f"{spec[0]}: {np.sum(got.view(np.uint32) != exp.view(np.uint32))} of {len(xs)} samples differ"
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_tile_shapes_by_image_size(dtype):
+    """The default tile shape depends on the image size: small images take smaller tiles that
+    fill the GPU in one wave, 1024^2 keeps the large-image shapes. Both are checked against the
+    oracle (whole small images; sampled pixels, tile borders included, at 1024^2)."""
+    import torch
+    import paper_2505_22938_gb300 as fim
+    from helpers import to_device, to_host
+    code = {"u8": fim.FIM_U8, "u16": fim.FIM_U16, "f32": fim.FIM_F32}[dtype]
+    for r in (4, 16, 24, 32):
+        k = fim.fim_create_kernel_circle(r)
+        small = fim.fim_plan_info(k, code, 256, 256)
+        big = fim.fim_plan_info(k, code, 1024, 1024)
+        assert (small["tile_w"], small["tile_h"]) in ((32, 8), (32, 16)), (r, small)
+        assert big["tile_w"] * big["tile_h"] >= 1024, (r, big)
+    img = datagen.image_for(dtype, 811, 256, 256)
+    for r in (4, 24):
+        run_case(img, "circle", r)
+    img = datagen.image_for(dtype, 812, 1024, 1024)
+    store, _ = to_device(img)
+    out = torch.empty_like(store)
+    rng = np.random.default_rng(5)
+    edges = np.array([0, 31, 32, 63, 64, 127, 128, 1023])
+    xs = np.concatenate([rng.integers(0, 1024, 600), edges, rng.integers(0, 1024, 8)])
+    ys = np.concatenate([rng.integers(0, 1024, 600), rng.integers(0, 1024, 8), edges])
+    for r in (4, 16, 32):
+        fim.median(store, fim.fim_create_kernel_circle(r), out=out)
+        torch.cuda.synchronize()
+        assert fim.fim_sync_status() == 0
+        got = to_host(out)[ys, xs]
+        exp = oracle.median_points(img, oracle.disk_offsets(r), xs.astype(np.int32), ys.astype(np.int32))
+        assert np.array_equal(np.ascontiguousarray(got).view(np.uint8), np.ascontiguousarray(exp).view(np.uint8)), r
