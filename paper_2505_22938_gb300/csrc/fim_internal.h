@@ -238,9 +238,10 @@ void get_phase_clock_buffer(unsigned long long** buf, int* tiles);
 // staging region and the image allows them (16-byte aligned base and pitch); sets use_tma.
 void attach_tma(Plan& p);
 // Small images (w x h; 0 x 0: unknown, e.g. batches) whose tiles of the default shape `def`
-// would fill under half the GPU's resident CTAs, for kernels up to 65 pixels across: the first
-// of the smaller shapes 32x8 (4 bands), 32x16 (4 bands), 32x8 (2 bands) whose tiles all fit in
-// one wave of resident CTAs, in *out (true). `scratch` is storage for trial plans.
+// would fill under half the GPU's resident CTAs: the first of the smaller shapes (kernels up
+// to 65 pixels across: 32x8 with 4 bands, 32x16 with 4, 32x8 with 2; larger kernels: 32x16 and
+// 64x32 with 8 bands) whose tiles all fit in one wave of resident CTAs, in *out (true).
+// `scratch` is storage for trial plans.
 bool small_image_shape(const fim_kernel* k, int dtype, int w, int h, int smem_limit, int cta_threads,
                        bool exact_ranks, const TileShape& def, Plan* scratch, TileShape* out);
 

@@ -259,7 +259,9 @@ fim_status run_filter(const void* in, void* out, int w, int h, size_t pitch, int
     const int limit = device_smem_limit();
     if (limit <= 0) return FIM_ERR_CUDA;
     TileShape ts;
-    fim_status s = choose_tile(k, dtype, limit, &ts, w, h);
+    // the bracket's features and labels depend on the tile geometry, so training rows and the
+    // learned launches take the large-image shapes whatever the image size
+    fim_status s = choose_tile(k, dtype, limit, &ts, 0, 0);
     if (s != FIM_OK) return s;
     Plan* p = new (std::nothrow) Plan;
     if (!p) return FIM_ERR_OOM;

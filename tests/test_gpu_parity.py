@@ -235,9 +235,15 @@ def test_tile_shapes_by_image_size(dtype):
         big = fim.fim_plan_info(k, code, 1024, 1024)
         assert (small["tile_w"], small["tile_h"]) in ((32, 8), (32, 16)), (r, small)
         assert big["tile_w"] * big["tile_h"] >= 1024, (r, big)
+    for r in (48, 96):
+        k = fim.fim_create_kernel_circle(r)
+        small = fim.fim_plan_info(k, code, 256, 256)
+        assert (small["tile_w"], small["tile_h"]) in ((32, 16), (64, 32)), (r, small)
     img = datagen.image_for(dtype, 811, 256, 256)
     for r in (4, 24):
         run_case(img, "circle", r)
+    img = datagen.image_for(dtype, 813, 200, 184)
+    run_case(img, "circle", 48)
     img = datagen.image_for(dtype, 812, 1024, 1024)
     store, _ = to_device(img)
     out = torch.empty_like(store)
