@@ -43,7 +43,8 @@ typedef enum {
     FIM_ERR_UNSUPPORTED = 2, /* valid request this build cannot serve (e.g. kernel too large) */
     FIM_ERR_OOM = 3,         /* device or host allocation failed */
     FIM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
-    FIM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (persistent batch queue) */
+    FIM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (a footprint copy's mbarrier;
+                                the output is still exact: the tile read the image instead) */
     FIM_ERR_INTERNAL = 6     /* a device-side consistency check failed */
 } fim_status;
 
@@ -96,7 +97,10 @@ void fim_destroy_kernel(fim_kernel* k);
 
 /*
  * Median filter (Sec. 3.3 steps 1-7). in/out: device images of w x h elements of `dtype`,
- * rows pitch_bytes apart. w, h >= 1. Asynchronous on `stream`.
+ * rows pitch_bytes apart. w, h >= 1. Asynchronous on `stream`. The tile configuration is the
+ * autotuned one for the kernel geometry and image-size class where fim_autotune ran, else a
+ * default by kernel extent; images too small to fill the GPU with the default tiles take
+ * smaller ones that fit in one wave of resident CTAs. Results do not depend on the tiling.
  */
 fim_status fim_median(const void* in, void* out, int w, int h, size_t pitch_bytes, fim_dtype dtype,
                       const fim_kernel* k, fim_border border, void* stream);
@@ -214,9 +218,11 @@ fim_status fim_autotune_clear(void);
 /*
  * Batched persistent launch. One job is one 2-D image filtered with its own kernel, dtype, size
  * and pitch; percentile < 0 selects the median, otherwise the percentile filter of fim_percentile.
- * One persistent launch works off every job: each CTA visits the jobs in order of decreasing
- * cost per tile, and its tile groups (1024 / the job's CTA size of them) take that job's tiles
- * from the job's own device-side counter until none are left. Not part of the paper.
+ * The jobs are grouped into classes by the pipeline they run (dtype, kernel shape, omnigram
+ * encoding and home, scan width) and CTA size. Each class is one persistent kernel whose CTAs
+ * take tiles from one device-side queue over the tiles of all the class's jobs (expensive tiles
+ * first); a class of one job runs the single-image kernel on that job. The classes run side by
+ * side on the batch's own streams, forked from and joined to the caller's. Not part of the paper.
  */
 typedef struct {
     const void* in;      /* device pointer */
@@ -239,11 +245,14 @@ typedef struct fim_batch fim_batch;
  */
 fim_status fim_batch_create(const fim_job* jobs, int count, fim_batch** out);
 
-/* Runs a batch on `stream`: one memset of the per-job tile counters and one kernel launch, both
- * stream operations (graph-capturable). Runs of one batch must not overlap in time. */
+/* Runs a batch on `stream`: one memset of the class queue counters, then per class a kernel
+ * launch on the caller's stream or one of the batch's streams (event fork and join): stream
+ * operations and host-side launch set-up only, so a run can be captured into a CUDA graph.
+ * Runs of one batch must not overlap in time. */
 fim_status fim_batch_run(fim_batch* b, void* stream);
 
-/* Size of a batch launch: total queued tiles, CTAs, threads per CTA, shared memory per CTA. */
+/* Size of a batch run: total queued tiles, CTAs over all class kernels, and the largest CTA
+ * size and shared memory per CTA among them. */
 fim_status fim_batch_info(const fim_batch* b, int* total_tiles, int* grid, int* threads, int* smem_bytes);
 
 /* Waits for the device, then frees the batch (NULL is ignored). */
