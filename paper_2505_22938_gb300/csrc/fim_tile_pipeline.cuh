@@ -1301,9 +1301,23 @@ __device__ __forceinline__ void process_tile(const Plan& P, int tile, unsigned c
 
     // ---- 2. ordinal image I (Eq. 4) ------------------------------------------------------------
     stamp(P, tile, 2, G);
-    for (int v = tid; v < N; v += nthreads) {
-        const uint32_t e = om[v];
-        ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)clampi(v - rb, 0, 65535);
+    if constexpr (OG) {  // omnigram in global scratch: four entries per thread in flight
+        for (int v0 = tid; v0 < N; v0 += 4 * nthreads) {
+            uint32_t e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[k] = v0 + k * nthreads < N ? (uint32_t)om[v0 + k * nthreads] : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int v = v0 + k * nthreads;
+                if (v < N)
+                    ord[(Loc<W>::y(e[k]) + cy0) * SP + Loc<W>::x(e[k]) + cx0] = (uint16_t)clampi(v - rb, 0, 65535);
+            }
+        }
+    } else {
+        for (int v = tid; v < N; v += nthreads) {
+            const uint32_t e = om[v];
+            ord[(Loc<W>::y(e) + cy0) * SP + Loc<W>::x(e) + cx0] = (uint16_t)clampi(v - rb, 0, 65535);
+        }
     }
     {   // pad the last 128-bit group with sentinels no window contains
         const int pad = ((N + Loc<W>::kGroup - 1) & ~(Loc<W>::kGroup - 1)) - N;
