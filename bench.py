@@ -192,9 +192,9 @@ def algorithmic_ops_per_pixel(r: int, footprint: int, tile_w: int, tile_h: int, 
 def sort_passes(dtype: str, threads: int, footprint: int = 0) -> int:
     """Key passes of the ordinal transform the library runs for a plan (see the docstring above);
     footprints beyond 65535 pixels overflow the 16-bit counters of the 65536-bin pass: 16-bit
-    data counts in two rounds, float keys take four 8-bit passes."""
-    if dtype == "f32":  # full CTAs: one 16-bit counting pass + two 8-bit passes
-        return 3 if threads >= 1024 and footprint <= 65535 else 4
+    data and the float keys' 16-bit pass count in two rounds of the same pass."""
+    if dtype == "f32":  # full CTAs: one 16-bit counting pass (two rounds beyond 65535) + two 8-bit passes
+        return 3 if threads >= 1024 else 4
     if dtype == "u16" and threads < 1024:
         return 2
     if dtype == "u16" and footprint > 65535:  # the counting sort in two rounds over the key range

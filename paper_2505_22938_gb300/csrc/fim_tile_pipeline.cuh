@@ -849,6 +849,10 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     // nthreads, ... (coalesced rows), four loads in flight, and counts the low digit (8 bits in its
     // warp's histogram, or 16 bits in the block's packed bins); equal digits may then land in any
     // order (returned atomics), since the later passes are stable.
+    // Footprints of more than 65535 pixels would overflow the packed 16-bit counters: the 16-bit
+    // pass then counts in two rounds over the digit range (top bit 0, then 1), each with 32768
+    // 32-bit bins in the same 128 KiB (the first round's histogram fused with the load).
+    const bool two = C16 && P.N > 65535;
     if constexpr (C16) {
         for (int i = tid * 4; i < 32768; i += nthreads * 4)
             *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
@@ -874,10 +878,15 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
         for (int k = 0; k < 4; ++k)
             if (in[k]) {
                 keys[i0 + k * nthreads] = key[k];
-                if constexpr (C16)
-                    atomicAdd(&bins[(key[k] & 0xffffu) >> 1], 1u << ((key[k] & 1u) << 4));
-                else
+                if constexpr (C16) {
+                    const uint32_t d = key[k] & 0xffffu;
+                    if (!two)
+                        atomicAdd(&bins[d >> 1], 1u << ((d & 1u) << 4));
+                    else if ((d >> 15) == 0)
+                        atomicAdd(&bins[d], 1u);
+                } else {
                     atomicAdd(&hw[key[k] & 0xff], 1u);
+                }
             }
     }
     G.sync();
@@ -887,13 +896,54 @@ __device__ void ordinal_transform_radix(const Plan& P, const int* frow, uint32_t
     // The keys may live in global scratch: every loop below loads kG of them (all in flight)
     // before it uses the first.
     constexpr int kG = 4;
-    if constexpr (C16)
-        scan_bins16(bins, wsum, P, G);
-    else {
+    if constexpr (C16) {
+        if (two) {
+            uint32_t base = 0;
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1) {  // the second round's histogram (the keys, in order, from scratch)
+                    for (int i = tid * 4; i < 32768; i += nthreads * 4)
+                        *reinterpret_cast<uint4*>(bins + i) = make_uint4(0, 0, 0, 0);
+                    G.sync();
+                    for (int i0 = tid; i0 < area; i0 += kG * nthreads) {
+                        uint32_t key[kG];
+                        bool in[kG];
+#pragma unroll
+                        for (int k = 0; k < kG; ++k) {
+                            const int i = i0 + k * nthreads;
+                            in[k] = i < area && inside(i);
+                            key[k] = in[k] ? keys[i] & 0xffffu : 0u;
+                        }
+#pragma unroll
+                        for (int k = 0; k < kG; ++k)
+                            if (in[k] && (key[k] >> 15) == 1u) atomicAdd(&bins[key[k] & 0x7fffu], 1u);
+                    }
+                    G.sync();
+                }
+                base += scan_bins32(bins, wsum, base, P, G);
+                for (int i0 = tid; i0 < area; i0 += kG * nthreads) {
+                    uint32_t key[kG];
+                    bool in[kG];
+#pragma unroll
+                    for (int k = 0; k < kG; ++k) {
+                        const int i = i0 + k * nthreads;
+                        in[k] = i < area && inside(i);
+                        key[k] = in[k] ? keys[i] & 0xffffu : 0u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kG; ++k)
+                        if (in[k] && (key[k] >> 15) == (uint32_t)h)
+                            first[atomicAdd(&bins[key[k] & 0x7fffu], 1u)] = (Pos)(i0 + k * nthreads);
+                }
+                G.sync();
+            }
+        } else {
+            scan_bins16(bins, wsum, P, G);
+        }
+    } else {
         scan_counts();
         G.sync();
     }
-    for (int i0 = tid; i0 < area; i0 += kG * nthreads) {
+    for (int i0 = tid; i0 < area && !two; i0 += kG * nthreads) {
         uint32_t key[kG];
         bool in[kG];
 #pragma unroll

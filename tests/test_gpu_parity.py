@@ -258,3 +258,28 @@ def test_tile_shapes_by_image_size(dtype):
         got = to_host(out)[ys, xs]
         exp = oracle.median_points(img, oracle.disk_offsets(r), xs.astype(np.int32), ys.astype(np.int32))
         assert np.array_equal(np.ascontiguousarray(got).view(np.uint8), np.ascontiguousarray(exp).view(np.uint8)), r
+
+
+def test_f32_footprints_beyond_65535():
+    """Float keys whose tile footprint exceeds 65535 pixels (1024^2, disk r = 100 on 64x128 tiles,
+    r = 128 on 64x64): the 16-bit pass of the radix sort counts in two rounds. Sampled pixels,
+    tile borders included, against the oracle."""
+    import torch
+    import paper_2505_22938_gb300 as fim
+    from helpers import to_device, to_host
+    img = datagen.image_for("f32", 814, 1024, 1024)
+    store, _ = to_device(img)
+    out = torch.empty_like(store)
+    rng = np.random.default_rng(8)
+    edges = np.array([0, 63, 64, 127, 128, 511, 512, 1023])
+    xs = np.concatenate([rng.integers(0, 1024, 300), edges, rng.integers(0, 1024, 8)])
+    ys = np.concatenate([rng.integers(0, 1024, 300), rng.integers(0, 1024, 8), edges])
+    for r in (100, 128):
+        k = fim.fim_create_kernel_circle(r)
+        assert fim.fim_plan_info(k, fim.FIM_F32, 1024, 1024)["footprint"] > 65535
+        fim.median(store, k, out=out)
+        torch.cuda.synchronize()
+        assert fim.fim_sync_status() == 0
+        got = to_host(out)[ys, xs]
+        exp = oracle.median_points(img, oracle.disk_offsets(r), xs.astype(np.int32), ys.astype(np.int32))
+        assert np.array_equal(np.ascontiguousarray(got).view(np.uint32), np.ascontiguousarray(exp).view(np.uint32)), r
